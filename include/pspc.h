@@ -1,0 +1,169 @@
+/*
+ * pspc.h -- C ABI of the GB300 shortest-path-counting (SPC) hub-label
+ * library: parallel construction of the 2-hop SPC index of an undirected,
+ * unweighted graph, and batched SPC(s,t) queries on it.
+ *
+ * Paper: "PSPC: Efficient Parallel Shortest Path Counting on Large-Scale
+ * Graphs" (Peng, Yu, Wang; arXiv 2212.00977).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Vertices are ids 0..n-1 chosen by the caller. The caller also supplies a
+ *   total order as rank[v] in [0,n), a permutation, rank 0 = highest (the
+ *   order "w <= v means w ranks higher" of Section "PSPC algorithm
+ *   description from the Covering Side").
+ * - Label entries are (hub, dist, count, overflow): dist = sd(v,hub) is exact,
+ *   count = the number of trough shortest paths between v and hub (hub ranked
+ *   above every other vertex on them) modulo 2^64, overflow = 1 iff that
+ *   exact number is >= 2^64. Query counts follow the same rule.
+ * - Pointers may be host or device memory unless stated otherwise; the
+ *   library detects which with cudaPointerGetAttributes and stages host
+ *   buffers through device memory inside the call (host <-> device copies
+ *   are then part of the call).
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream). Calls return after their work on `stream` has completed.
+ * - Every entry point returns an int status (PSPC_OK = 0); no exception or
+ *   longjmp crosses this boundary. pspc_strerror() names a status.
+ * - Only one GPU is used: the device current on the calling thread when
+ *   pspc_build is called; later calls on that index switch to it.
+ */
+#ifndef PSPC_H
+#define PSPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define PSPC_OK 0
+#define PSPC_E_INVAL 1   /* malformed graph, rank, pair or argument */
+#define PSPC_E_NOMEM 2   /* device or host allocation failed */
+#define PSPC_E_CUDA 3    /* a CUDA runtime call or kernel failed */
+#define PSPC_E_TIMEOUT 4 /* a bounded device-side wait gave up */
+#define PSPC_E_DIST 5    /* a shortest distance exceeds 32767 */
+
+/* Unreachable marker in query and export distances. */
+#define PSPC_UNREACHED 0xFFFFu
+
+/* Undirected graph as symmetric CSR over caller vertex ids.
+ * row_ptr: int64[n+1], row_ptr[0] = 0, non-decreasing.
+ * col:     int32[row_ptr[n]]; the neighbours of v are col[row_ptr[v] ..
+ *          row_ptr[v+1]), strictly ascending (so no duplicate arcs), no
+ *          self-loop, and every arc u->v has its reverse v->u.
+ * 1 <= n < 2^24. Violations make pspc_build return PSPC_E_INVAL. */
+typedef struct {
+    int64_t n;
+    const int64_t* row_ptr;
+    const int32_t* col;
+} pspc_csr;
+
+/* Build options; pass NULL for defaults. Zero fields take their default. */
+typedef struct {
+    int32_t cand_capacity;   /* on-chip candidate hash slots per vertex
+                                (power of two, 1024..16384; default 4096) */
+    int32_t label_capacity;  /* on-chip label hash slots per vertex (power of
+                                two, 1024..16384; default 8192) */
+    int64_t arena_entries;   /* initial label arena capacity in entries
+                                (default 64 * n; grows on demand) */
+    int32_t max_levels;      /* stop with PSPC_E_DIST after this many levels
+                                (default 32767) */
+    int32_t verbose;         /* 1: per-level line on stderr */
+} pspc_opts;
+
+/* Per-level counters of the last build (level d = distance d). */
+typedef struct {
+    int64_t raw_candidates;    /* pulled entries (h, d-1, c) with h above u */
+    int64_t unique_candidates; /* distinct (u, h) after count merging */
+    int64_t entries;           /* survivors appended as level d */
+    int64_t active_vertices;   /* vertices with at least one pulled entry */
+    float ms;                  /* device time of the level */
+} pspc_level_stats;
+
+typedef struct {
+    int64_t n;
+    int64_t arcs;        /* directed arcs = 2m */
+    int64_t entries;     /* total label entries */
+    int32_t levels;      /* number of non-empty levels (max distance + 1) */
+    int32_t device;      /* CUDA device ordinal holding the index */
+    int64_t index_bytes; /* device bytes held by the finished index */
+    int64_t overflow_entries; /* entries whose exact count is >= 2^64 */
+    float build_ms;      /* device time of pspc_build, input checks included */
+} pspc_stats_t;
+
+typedef struct pspc_index pspc_index;
+
+/*
+ * pspc_build -- construct the SPC hub-label index of g under `rank`.
+ *
+ * Computes, for every vertex v, L(v) = {(w, sd(v,w), tau(v,w))} over w = v
+ * and the vertices w ranked above v with tau(v,w) > 0, where tau counts the
+ * trough shortest paths (the ESPC construction of Section "PSPC algorithm
+ * description from the Covering Side"; by Theorem "L^SPC = L^PSPC" this is
+ * the index of the sequential hub-pushing method).
+ * Method: level-synchronous pull propagation by distance d (Theorem
+ * "Distance Dependency", Lemma "Propagation", Algorithm PULL): each vertex u
+ * gathers its neighbours' level-(d-1) entries whose hub ranks above u
+ * (pruning rule 1), merges counts per hub (Label Merging), drops hubs for
+ * which a query over the labels of distance < d gives a shorter distance
+ * (pruning rule 2), and appends the rest as level d. The build stops after
+ * the first level with no entry.
+ *
+ * g, rank:  host or device memory, borrowed for the call only.
+ * opts:     NULL or host pointer.
+ * out:      host pointer; receives an index owned by the library until
+ *           pspc_free. On failure *out is set to NULL.
+ * Errors:   PSPC_E_INVAL (bad CSR or rank, n out of range), PSPC_E_NOMEM,
+ *           PSPC_E_CUDA, PSPC_E_DIST (distance above 32767 or max_levels).
+ */
+int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opts* opts,
+               pspc_index** out, void* stream);
+
+/*
+ * pspc_query -- answer q SPC(s,t) queries (Eq. (1)-(2)): over the common
+ * hubs h of L(s) and L(t), dist = min sd(s,h) + sd(h,t) and count = sum of
+ * tau(s,h) * tau(h,t) over the hubs reaching that minimum, modulo 2^64;
+ * overflow = 1 iff the exact count is >= 2^64.
+ *
+ * pairs: int32[q][2] caller vertex ids (s, t), host or device.
+ * dist:  uint16[q] out; PSPC_UNREACHED when s and t are not connected.
+ * count: uint64[q] out; 0 when unreachable; SPC(s,s) = (0, 1).
+ * overflow: uint8[q] out (may be NULL).
+ * Outputs are caller-allocated, host or device (all of one kind).
+ * q = 0 is a no-op. Errors: PSPC_E_INVAL (NULL index/pointer, q < 0, a
+ * vertex id outside [0,n); outputs are then unspecified), PSPC_E_CUDA,
+ * PSPC_E_NOMEM.
+ */
+int pspc_query(const pspc_index* ix, const int32_t* pairs, int64_t q, uint16_t* dist,
+               uint64_t* count, uint8_t* overflow, void* stream);
+
+/*
+ * pspc_export -- copy the index to host arrays, by caller vertex id, each
+ * label listed by hub rank (highest first), hubs given as caller ids.
+ * off: int64[n+1]; hub: int32[E]; dist: uint16[E]; cnt: uint64[E];
+ * ovf: uint8[E] (E = pspc_stats().entries). All host memory owned by the
+ * caller. Errors: PSPC_E_INVAL, PSPC_E_NOMEM, PSPC_E_CUDA.
+ */
+int pspc_export(const pspc_index* ix, int64_t* off, int32_t* hub, uint16_t* dist,
+                uint64_t* cnt, uint8_t* ovf);
+
+/* pspc_stats -- sizes and timings of an index (host struct). */
+int pspc_stats(const pspc_index* ix, pspc_stats_t* s);
+
+/* pspc_level_stats -- copy up to `cap` per-level records (level 1 first) to
+ * host memory; *levels receives the number of levels built after level 0. */
+int pspc_level_stats(const pspc_index* ix, pspc_level_stats* out, int32_t cap,
+                     int32_t* levels);
+
+/* pspc_free -- release an index and all its device memory; NULL is a no-op. */
+void pspc_free(pspc_index* ix);
+
+/* pspc_strerror -- static, human-readable name of a status code. */
+const char* pspc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSPC_H */
