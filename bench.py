@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the SPC hub-label path on GB300.
+
+One step = one full pass of the path on the R-MAT scale-16 workload:
+pspc_build (rank relabel, level-synchronous pull construction, finalize)
+followed by pspc_query on 10^6 uniform (s,t) pairs. Inputs are resident in
+device memory before the timed region; L2 is flushed (256 MiB write)
+between steps. Times are CUDA events on the launching stream.
+
+Prints one JSON line. ``value`` is label entries per second of the build
+(whole job: summed over ranks, divided by the slowest rank's time); query
+throughput is reported beside it. ``--impl reference`` times the CPU oracle
+(the sequential hub-pushing labeler) on a bounded sample of the same
+workload instead.
+
+Multi-GPU: the path does not shard without an exchange step, so N ranks run
+N independent replicas (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ORACLE_SAMPLE_HUBS = 320  # bounded CPU sample: the 320 highest-ranked hubs
+WORKLOAD_DESC = {
+    "rmat16": ("R-MAT scale 16 (65,536 vertices), edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
+               "seed 1, symmetrised, self-loops and duplicates removed, degree-descending rank "
+               "(ties by id), int32 CSR; index build + 10^6 uniform random (s,t) pairs (seed 2)"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="rmat16")
+    ap.add_argument("--queries", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) of SM clocks and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pspc_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 r[2:]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def level_kernel_traffic():
+    """DRAM bytes per launch of the level kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_level_rmat16.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = os.path.join(ROOT, "paper_2212_00977_gb300", "csrc", "pspc_build.cu")
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != d.get("source_sha256"):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def level_algorithmic_bytes(ls):
+    """Bytes any pull implementation must move at one level: the CSR arcs of
+    the active vertices (4 B), every pulled entry (hub 4 B + count 8 B) and
+    every appended entry (12 B). The prune reads are not counted."""
+    return 4 * ls["active_arcs"] + 12 * ls["raw_candidates"] + 12 * ls["entries"]
+
+
+def cpu_baseline(g, rank, hubs=ORACLE_SAMPLE_HUBS):
+    import oracle
+
+    t0 = time.perf_counter()
+    ix = oracle.OracleIndex(g, rank, max_hubs=hubs)
+    dt = time.perf_counter() - t0
+    return ix.entries, dt
+
+
+def run_reference(args):
+    rank_id, _, world = dist_info()
+    if rank_id != 0:
+        return 0
+    import pspc_inputs as P
+
+    g, rank, _ = P.workload(args.workload)
+    for _ in range(args.warmup):
+        cpu_baseline(g, rank)
+    ent, times = 0, []
+    for _ in range(args.steps):
+        e, dt = cpu_baseline(g, rank)
+        ent = e
+        times.append(dt)
+    T = sum(times)
+    value = ent * len(times) / T
+    sample = (f"hub-pushing labeler (C, 1 thread) over the {ORACLE_SAMPLE_HUBS} highest-ranked hubs of "
+              f"the {args.workload} graph: {ent} of its label entries per step")
+    line = {"impl": "reference", "metric": "label entries/s (index build)", "value": value, "unit": "entries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * T / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "entries/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2212_00977_gb300 as pspc
+    import pspc_inputs as P
+
+    rank_id, local_rank, world = dist_info()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    pspc.load()
+
+    g, rank, pairs_fn = P.workload(args.workload)
+    pairs = pairs_fn(args.queries)
+    rp_d = torch.from_numpy(g.row_ptr).to(dev)
+    col_d = torch.from_numpy(g.col).to(dev)
+    rk_d = torch.from_numpy(rank).to(dev)
+    pairs_d = torch.from_numpy(pairs).to(dev)
+    q = len(pairs)
+    out_d = torch.empty(q, dtype=torch.uint16, device=dev)
+    out_c = torch.empty(q, dtype=torch.uint64, device=dev)
+    out_f = torch.empty(q, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(timed):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix = pspc.Index.build(g.n, rp_d, col_d, rk_d, stream=stream)
+        e1.record(stream)
+        ix.query(pairs_d, out_d, out_c, out_f, stream=stream)
+        e2.record(stream)
+        e2.synchronize()
+        st = ix.stats()
+        ls = ix.level_stats()
+        ix.free()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), st, ls
+
+    for _ in range(max(args.warmup, 0)):
+        step(False)
+    sampler = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    res = [step(True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+
+    build_ms = [r[0] for r in res]
+    query_ms = [r[1] for r in res]
+    st = res[-1][2]
+    entries = st["entries"]
+    launches_per_step = st["kernel_launches"] + 1
+    T_build = sum(build_ms)
+    T_query = sum(query_ms)
+    T_step = T_build + T_query
+    if dist:
+        t = torch.tensor([T_build, T_query, T_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T_build, T_query, T_step = t.tolist()
+    K = args.steps
+    value = world * K * entries / (T_build / 1e3)
+    qps = world * K * q / (T_query / 1e3)
+
+    # roofline of the level kernel (gather / merge / prune / append)
+    kb = sum(level_algorithmic_bytes(l) for r in res for l in r[3])
+    kms = sum(l["kernel_ms"] for r in res for l in r[3])
+    klaunch = sum(1 for r in res for l in r[3] if l["kernel_ms"] > 0)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = kb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    traffic = level_kernel_traffic()
+
+    line = {"metric": "label entries/s (index build)", "value": value, "unit": "entries/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": T_step / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "n": g.n, "arcs": g.arcs,
+                       "queries_per_step": q, "l2": "flushed: 256 MiB device write before every step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "build_ms": T_build / K, "query_ms": T_query / K, "queries_per_s": qps,
+            "entries": entries, "levels": st["levels"],
+            "roofline": {"kernel": "k_level (pull gather + count merge + prune + append)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if peak else None,
+                         "peak_kind": peak_kind,
+                         "traffic": traffic,
+                         "bytes_per_step": kb / K, "kernel_ms_per_step": kms / K,
+                         "launches_per_step": klaunch / K},
+            "gpu_launches": launches_per_step * K,
+            "clocks": clocks}
+
+    if rank_id == 0 and world == 1:
+        # end to end through the public API with host buffers
+        e2e_b, e2e_q = [], []
+        h2d = g.row_ptr.nbytes + g.col.nbytes + rank.nbytes + pairs.nbytes
+        d2h = q * (2 + 8 + 1)
+        for i in range(args.e2e_steps + 1):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ix = pspc.Index.from_graph(g, rank)
+            t1 = time.perf_counter()
+            d, c, f = ix.query(pairs)
+            t2 = time.perf_counter()
+            ix.free()
+            if i:  # first one is a warm-up
+                e2e_b.append(t1 - t0)
+                e2e_q.append(t2 - t1)
+        line["e2e"] = {"value": entries / statistics.mean(e2e_b), "unit": "entries/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "queries_per_s": q / statistics.mean(e2e_q),
+                       "step_s": statistics.mean(e2e_b) + statistics.mean(e2e_q)}
+        if not args.no_cpu_baseline:
+            ent, dt = cpu_baseline(g, rank)
+            line["cpu_baseline"] = {
+                "value": ent / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
+                "sample": (f"hub-pushing labeler (C, 1 thread) over the {ORACLE_SAMPLE_HUBS} highest-ranked "
+                           f"hubs of the same graph: {ent} label entries in {dt:.1f} s")}
+    if rank_id == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -78,8 +78,11 @@ typedef struct {
     int64_t unique_candidates; /* distinct (u, h) after count merging */
     int64_t entries;           /* survivors appended as level d */
     int64_t active_vertices;   /* vertices with at least one pulled entry */
-    float ms;                  /* device time of the level */
-} pspc_level_stats;
+    int64_t active_arcs;       /* CSR arcs of those vertices */
+    float ms;                  /* device time of the whole level */
+    float kernel_ms;           /* device time of the level's gather/merge/
+                                  prune/append kernel launches only */
+} pspc_level_stat_t;
 
 typedef struct {
     int64_t n;
@@ -89,6 +92,7 @@ typedef struct {
     int32_t device;      /* CUDA device ordinal holding the index */
     int64_t index_bytes; /* device bytes held by the finished index */
     int64_t overflow_entries; /* entries whose exact count is >= 2^64 */
+    int64_t kernel_launches; /* CUDA kernels launched by pspc_build */
     float build_ms;      /* device time of pspc_build, input checks included */
 } pspc_stats_t;
 
@@ -153,7 +157,7 @@ int pspc_stats(const pspc_index* ix, pspc_stats_t* s);
 
 /* pspc_level_stats -- copy up to `cap` per-level records (level 1 first) to
  * host memory; *levels receives the number of levels built after level 0. */
-int pspc_level_stats(const pspc_index* ix, pspc_level_stats* out, int32_t cap,
+int pspc_level_stats(const pspc_index* ix, pspc_level_stat_t* out, int32_t cap,
                      int32_t* levels);
 
 /* pspc_free -- release an index and all its device memory; NULL is a no-op. */

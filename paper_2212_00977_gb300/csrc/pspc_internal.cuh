@@ -1,0 +1,77 @@
+// Internal definitions shared by the CUDA translation units of the SPC
+// hub-label library (index layout, level-segment encoding, small device
+// helpers). Not part of the public ABI (include/pspc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "pspc.h"
+
+namespace pspc {
+
+// Vertex and hub ids are rank positions (0 = highest rank) inside the
+// library; n < 2^24, so an id fits in 24 bits.
+constexpr uint32_t kHubMask = 0x00FFFFFFu;
+constexpr uint32_t kOvfBit = 0x80000000u;   // overflow flag carried with a hub word
+constexpr uint32_t kMarkBit = 0x40000000u;  // survivor mark inside candidate tables
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;    // empty hash slot
+constexpr int64_t kMaxVertices = (1 << 24) - 1;
+constexpr int kMaxDist = 32767;
+
+// A level segment of one vertex: the entries of L_d(u) live at
+// [start, start + len) of the label arena. start < 2^40, len < 2^24.
+__host__ __device__ inline uint64_t seg_pack(uint64_t start, uint32_t len) {
+    return (start << 24) | (uint64_t)len;
+}
+__host__ __device__ inline uint64_t seg_start(uint64_t s) { return s >> 24; }
+__host__ __device__ inline uint32_t seg_len(uint64_t s) { return (uint32_t)(s & 0xFFFFFFu); }
+
+__host__ __device__ inline uint32_t hash_hub(uint32_t h) { return h * 0x9E3779B1u; }
+
+__host__ __device__ inline uint32_t pow2_ceil(uint64_t x) {
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Finished index (all device memory, ids in rank space).
+struct Index {
+    int device = 0;
+    int64_t n = 0, arcs = 0;
+    int32_t* rank = nullptr;   // caller id -> rank id
+    int32_t* order = nullptr;  // rank id -> caller id
+    int64_t* off = nullptr;    // [n+1]
+    int32_t* hub = nullptr;    // hub rank ids
+    uint16_t* dist = nullptr;  // distance | overflow << 15
+    uint64_t* cnt = nullptr;   // trough path count mod 2^64
+    int64_t entries = 0;
+    int32_t levels = 0;
+    int64_t overflow_entries = 0;
+    float build_ms = 0.f;
+    int64_t launches = 0;
+    std::vector<pspc_level_stat_t> lstats;
+};
+
+// Host-side helpers (pspc_util.cu).
+bool is_device_ptr(const void* p);
+int cuda_status(cudaError_t e);
+
+// Exclusive prefix sum of int64 values in place: a[0..n) -> exclusive
+// scan, a[n] = total (a must hold n+1 values). Device memory.
+// *launches (if not NULL) is increased by the kernels launched.
+int exclusive_scan_i64(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches = nullptr);
+
+}  // namespace pspc
+
+struct pspc_index {
+    pspc::Index ix;
+};
+
+#define PSPC_TRY_CUDA(expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return pspc::cuda_status(_e);  \
+    } while (0)

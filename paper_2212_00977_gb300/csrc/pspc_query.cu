@@ -1,0 +1,226 @@
+// SPC(s,t) queries on the hub-label index: Eq. (1)-(2) of the paper
+// (Section "2-Hop Labeling for Shortest Path Counting"), evaluated as a
+// warp-cooperative merge-join of the two hub-sorted labels; queries are
+// independent (Section "Reduction by Equivalence Relation", parallel query
+// evaluation), so one warp answers one pair at a time.
+//
+// Per pair: each lane holds one hub of a 32-entry chunk of L(s) and looks
+// it up in the current 32-entry chunk of L(t) with a 5-step shuffle binary
+// search; the chunk whose last hub is smaller advances. A match h gives
+// dist_s(h) + dist_t(h); counts (and their 128-bit product) are read only
+// for matches that reach the lane's running minimum. The warp then keeps
+// the global minimum and adds the products of the hubs that reach it,
+// modulo 2^64, with a sticky overflow flag (flag of a factor, high word of
+// a product, carry of a sum).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "pspc_internal.cuh"
+
+namespace pspc {
+
+constexpr int kQueryThreads = 256;
+constexpr uint32_t kNoHub = 0xFFFFFFFFu;
+
+struct QueryArgs {
+    int64_t n;
+    const int32_t* rank;
+    const int64_t* off;
+    const int32_t* hub;
+    const uint16_t* dist;
+    const uint64_t* cnt;
+    const int32_t* pairs;
+    int64_t q;
+    uint16_t* out_dist;
+    uint64_t* out_cnt;
+    uint8_t* out_ovf;
+    int* err;
+};
+
+__device__ __forceinline__ void add_term(uint64_t& sum, uint32_t& flag, uint64_t term, uint32_t tflag) {
+    const uint64_t s = sum + term;
+    flag |= tflag | (uint32_t)(s < term);
+    sum = s;
+}
+
+__global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kQueryThreads / 32);
+    for (int64_t p = ((int64_t)blockIdx.x * kQueryThreads + threadIdx.x) >> 5; p < Q.q; p += warps) {
+        const int32_t s = __ldg(Q.pairs + 2 * p), t = __ldg(Q.pairs + 2 * p + 1);
+        if (s < 0 || s >= Q.n || t < 0 || t >= Q.n) {
+            if (lane == 0) {
+                atomicOr(Q.err, 1);
+                Q.out_dist[p] = PSPC_UNREACHED;
+                Q.out_cnt[p] = 0;
+                if (Q.out_ovf) Q.out_ovf[p] = 0;
+            }
+            continue;
+        }
+        if (s == t) {
+            if (lane == 0) {
+                Q.out_dist[p] = 0;
+                Q.out_cnt[p] = 1;
+                if (Q.out_ovf) Q.out_ovf[p] = 0;
+            }
+            continue;
+        }
+        const int32_t rs = __ldg(Q.rank + s), rt = __ldg(Q.rank + t);
+        int64_t ia = __ldg(Q.off + rs);
+        const int64_t ea = __ldg(Q.off + rs + 1);
+        int64_t ib = __ldg(Q.off + rt);
+        const int64_t eb = __ldg(Q.off + rt + 1);
+        uint32_t best = 0xFFFFFFFFu;
+        uint64_t sum = 0;
+        uint32_t flag = 0;
+        while (ia < ea && ib < eb) {
+            const bool va = ia + lane < ea, vb = ib + lane < eb;
+            const uint32_t ha = va ? (uint32_t)__ldg(Q.hub + ia + lane) : kNoHub;
+            const uint32_t hb = vb ? (uint32_t)__ldg(Q.hub + ib + lane) : kNoHub;
+            const uint16_t db = vb ? __ldg(Q.dist + ib + lane) : 0;
+            const int la = ea - ia > 32 ? 31 : (int)(ea - ia - 1);
+            const int lb = eb - ib > 32 ? 31 : (int)(eb - ib - 1);
+            const uint32_t amax = __shfl_sync(0xFFFFFFFFu, ha, la);
+            const uint32_t bmax = __shfl_sync(0xFFFFFFFFu, hb, lb);
+            // largest j with hb_j <= ha (hb is ascending over the lanes)
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t v = __shfl_sync(0xFFFFFFFFu, hb, j + step);
+                if (v <= ha) j += step;
+            }
+            const uint32_t hj = __shfl_sync(0xFFFFFFFFu, hb, j);
+            const uint16_t dj = __shfl_sync(0xFFFFFFFFu, db, j);
+            if (va && hj == ha) {
+                const uint16_t da = __ldg(Q.dist + ia + lane);
+                const uint32_t dsum = (uint32_t)(da & 0x7FFF) + (uint32_t)(dj & 0x7FFF);
+                if (dsum <= best) {
+                    const uint64_t ca = __ldg((const unsigned long long*)Q.cnt + ia + lane);
+                    const uint64_t cb = __ldg((const unsigned long long*)Q.cnt + ib + j);
+                    const uint64_t lo = ca * cb;
+                    const uint32_t tf = (uint32_t)(da >> 15) | (uint32_t)(dj >> 15) | (uint32_t)(__umul64hi(ca, cb) != 0);
+                    if (dsum < best) {
+                        best = dsum;
+                        sum = lo;
+                        flag = tf;
+                    } else {
+                        add_term(sum, flag, lo, tf);
+                    }
+                }
+            }
+            if (amax < bmax) {
+                ia += 32;
+            } else if (bmax < amax) {
+                ib += 32;
+            } else {
+                ia += 32;
+                ib += 32;
+            }
+        }
+        uint32_t gbest = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gbest = min(gbest, __shfl_xor_sync(0xFFFFFFFFu, gbest, o));
+        if (best != gbest) {
+            sum = 0;
+            flag = 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t os = __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            const uint32_t of = __shfl_xor_sync(0xFFFFFFFFu, flag, o);
+            add_term(sum, flag, os, of);
+        }
+        if (lane == 0) {
+            if (gbest == 0xFFFFFFFFu) {
+                Q.out_dist[p] = PSPC_UNREACHED;
+                Q.out_cnt[p] = 0;
+                if (Q.out_ovf) Q.out_ovf[p] = 0;
+            } else {
+                Q.out_dist[p] = (uint16_t)gbest;
+                Q.out_cnt[p] = sum;
+                if (Q.out_ovf) Q.out_ovf[p] = (uint8_t)(flag != 0);
+            }
+        }
+    }
+}
+
+}  // namespace pspc
+
+using namespace pspc;
+
+extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, uint16_t* dist, uint64_t* count,
+                          uint8_t* overflow, void* stream) {
+    if (!h || q < 0) return PSPC_E_INVAL;
+    if (q == 0) return PSPC_OK;
+    if (!pairs || !dist || !count) return PSPC_E_INVAL;
+    const Index& ix = h->ix;
+    cudaStream_t st = (cudaStream_t)stream;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != ix.device) PSPC_TRY_CUDA(cudaSetDevice(ix.device));
+    const bool dev_in = is_device_ptr(pairs);
+    const bool dev_out = is_device_ptr(dist);
+    if (dev_out != is_device_ptr(count) || (overflow && dev_out != is_device_ptr(overflow))) {
+        if (prev != ix.device) cudaSetDevice(prev);
+        return PSPC_E_INVAL;
+    }
+    int32_t* d_pairs = nullptr;
+    uint16_t* d_dist = nullptr;
+    uint64_t* d_cnt = nullptr;
+    uint8_t* d_ovf = nullptr;
+    int* d_err = nullptr;
+    int rc = PSPC_OK;
+    cudaError_t e = cudaMallocAsync((void**)&d_err, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess && !dev_in) {
+        e = cudaMallocAsync((void**)&d_pairs, (size_t)q * 8, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_pairs, pairs, (size_t)q * 8, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess && !dev_out) {
+        e = cudaMallocAsync((void**)&d_dist, (size_t)q * 2, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_cnt, (size_t)q * 8, st);
+        if (e == cudaSuccess && overflow) e = cudaMallocAsync((void**)&d_ovf, (size_t)q, st);
+    }
+    if (e == cudaSuccess) {
+        QueryArgs Q;
+        Q.n = ix.n;
+        Q.rank = ix.rank;
+        Q.off = ix.off;
+        Q.hub = ix.hub;
+        Q.dist = ix.dist;
+        Q.cnt = ix.cnt;
+        Q.pairs = dev_in ? pairs : d_pairs;
+        Q.q = q;
+        Q.out_dist = dev_out ? dist : d_dist;
+        Q.out_cnt = dev_out ? count : d_cnt;
+        Q.out_ovf = dev_out ? overflow : d_ovf;
+        Q.err = d_err;
+        int sms = 0, occ = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_query, kQueryThreads, 0);
+        const int64_t want = (q + kQueryThreads / 32 - 1) / (kQueryThreads / 32);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
+        k_query<<<grid, kQueryThreads, 0, st>>>(Q);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !dev_out) {
+        e = cudaMemcpyAsync(dist, d_dist, (size_t)q * 2, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(count, d_cnt, (size_t)q * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && overflow) e = cudaMemcpyAsync(overflow, d_ovf, (size_t)q, cudaMemcpyDeviceToHost, st);
+    }
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_status(e);
+    else if (herr) rc = PSPC_E_INVAL;
+    if (d_pairs) cudaFreeAsync(d_pairs, st);
+    if (d_dist) cudaFreeAsync(d_dist, st);
+    if (d_cnt) cudaFreeAsync(d_cnt, st);
+    if (d_ovf) cudaFreeAsync(d_ovf, st);
+    if (d_err) cudaFreeAsync(d_err, st);
+    if (prev != ix.device) cudaSetDevice(prev);
+    return rc;
+}

@@ -1,0 +1,209 @@
+// Host utilities of the SPC hub-label library: pointer classification,
+// status mapping, a device exclusive scan, and the small ABI entry points
+// (pspc_stats, pspc_level_stats, pspc_export, pspc_free, pspc_strerror).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pspc_internal.cuh"
+
+namespace pspc {
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return PSPC_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return PSPC_E_NOMEM;
+    }
+    return PSPC_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int64 (tile per block, recursive over tile sums).
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int64_t* a, int64_t n, int64_t* tile_sums) {
+    __shared__ int64_t warp_tot[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? a[base + i] : 0;
+        s += v[i];
+    }
+    int64_t incl = warp_incl_scan(s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t t = (lane < kScanThreads / 32) ? warp_tot[lane] : 0;
+        t = warp_incl_scan(t);
+        if (lane < kScanThreads / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int64_t run = incl - s + (warp ? warp_tot[warp - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) a[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == kScanThreads - 1 && tile_sums) tile_sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(int64_t* a, int64_t n, const int64_t* tile_offs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] += tile_offs[i / kScanTile];
+}
+
+static int scan_rec(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches) {
+    if (n <= 0) return PSPC_OK;
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_scan_tiles<<<1, kScanThreads, 0, st>>>(a, n, nullptr);
+        if (launches) *launches += 1;
+        return cuda_status(cudaGetLastError());
+    }
+    int64_t* sums = nullptr;
+    PSPC_TRY_CUDA(cudaMallocAsync(&sums, (size_t)tiles * sizeof(int64_t), st));
+    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(a, n, sums);
+    int rc = cuda_status(cudaGetLastError());
+    if (rc == PSPC_OK) rc = scan_rec(sums, tiles, st, launches);
+    if (rc == PSPC_OK) {
+        k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, n, sums);
+        rc = cuda_status(cudaGetLastError());
+    }
+    if (launches) *launches += 2;
+    cudaFreeAsync(sums, st);
+    return rc;
+}
+
+int exclusive_scan_i64(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches) {
+    PSPC_TRY_CUDA(cudaMemsetAsync(a + n, 0, sizeof(int64_t), st));
+    return scan_rec(a, n + 1, st, launches);
+}
+
+}  // namespace pspc
+
+using namespace pspc;
+
+extern "C" const char* pspc_strerror(int code) {
+    switch (code) {
+        case PSPC_OK: return "ok";
+        case PSPC_E_INVAL: return "invalid argument (graph, rank, pair or option)";
+        case PSPC_E_NOMEM: return "out of memory";
+        case PSPC_E_CUDA: return "CUDA error";
+        case PSPC_E_TIMEOUT: return "bounded device wait timed out";
+        case PSPC_E_DIST: return "distance limit exceeded";
+        default: return "unknown status";
+    }
+}
+
+extern "C" void pspc_free(pspc_index* h) {
+    if (!h) return;
+    Index& ix = h->ix;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ix.device);
+    cudaFree(ix.rank);
+    cudaFree(ix.order);
+    cudaFree(ix.off);
+    cudaFree(ix.hub);
+    cudaFree(ix.dist);
+    cudaFree(ix.cnt);
+    cudaSetDevice(prev);
+    delete h;
+}
+
+extern "C" int pspc_stats(const pspc_index* h, pspc_stats_t* s) {
+    if (!h || !s) return PSPC_E_INVAL;
+    const Index& ix = h->ix;
+    memset(s, 0, sizeof(*s));
+    s->n = ix.n;
+    s->arcs = ix.arcs;
+    s->entries = ix.entries;
+    s->levels = ix.levels;
+    s->device = ix.device;
+    s->index_bytes = (ix.n * 2 + (ix.n + 1) * 2) * 4 + ix.entries * (4 + 2 + 8);
+    s->overflow_entries = ix.overflow_entries;
+    s->kernel_launches = ix.launches;
+    s->build_ms = ix.build_ms;
+    return PSPC_OK;
+}
+
+extern "C" int pspc_level_stats(const pspc_index* h, pspc_level_stat_t* out, int32_t cap,
+                                int32_t* levels) {
+    if (!h || cap < 0 || (cap > 0 && !out)) return PSPC_E_INVAL;
+    const Index& ix = h->ix;
+    const int32_t L = (int32_t)ix.lstats.size();
+    if (levels) *levels = L;
+    for (int32_t i = 0; i < std::min(cap, L); ++i) out[i] = ix.lstats[i];
+    return PSPC_OK;
+}
+
+extern "C" int pspc_export(const pspc_index* h, int64_t* off, int32_t* hub, uint16_t* dist,
+                           uint64_t* cnt, uint8_t* ovf) {
+    if (!h || !off || (h->ix.entries > 0 && (!hub || !dist || !cnt || !ovf))) return PSPC_E_INVAL;
+    const Index& ix = h->ix;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ix.device);
+    const int64_t n = ix.n, E = ix.entries;
+    std::vector<int64_t> roff(n + 1);
+    std::vector<int32_t> rank(n), order(n), rhub(E);
+    std::vector<uint16_t> rdist(E);
+    std::vector<uint64_t> rcnt(E);
+    int rc = PSPC_OK;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(roff.data(), ix.off, (n + 1) * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(rank.data(), ix.rank, n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(order.data(), ix.order, n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && E) e = cudaMemcpy(rhub.data(), ix.hub, E * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && E) e = cudaMemcpy(rdist.data(), ix.dist, E * 2, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && E) e = cudaMemcpy(rcnt.data(), ix.cnt, E * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_status(e);
+    if (rc == PSPC_OK) {
+        int64_t p = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            off[v] = p;
+            const int32_t r = rank[v];
+            for (int64_t i = roff[r]; i < roff[r + 1]; ++i, ++p) {
+                hub[p] = order[rhub[i]];
+                dist[p] = (uint16_t)(rdist[i] & 0x7FFF);
+                ovf[p] = (uint8_t)(rdist[i] >> 15);
+                cnt[p] = rcnt[i];
+            }
+        }
+        off[n] = p;
+    }
+    cudaSetDevice(prev);
+    return rc;
+}

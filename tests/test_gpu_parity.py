@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA index and query answers equal the CPU oracle bit for
+bit (tolerance zero: every value is an integer). All calls go through the C
+ABI via the Python binding."""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import pspc_inputs as P
+from tests import _graphs as G
+
+pytestmark = pytest.mark.gpu
+
+M64 = 1 << 64
+
+
+@pytest.fixture(scope="module")
+def pspc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_00977_gb300 as lib
+
+    lib.load()
+    return lib
+
+
+def gpu_index(pspc, g, rank, device=True, **kw):
+    import torch
+
+    if device:
+        d = torch.device("cuda:0")
+        return pspc.Index.build(g.n, torch.from_numpy(g.row_ptr).to(d), torch.from_numpy(g.col).to(d),
+                                torch.from_numpy(np.ascontiguousarray(rank, np.int32)).to(d), **kw)
+    return pspc.Index.from_graph(g, rank, **kw)
+
+
+def assert_index_equal(ix, ref):
+    off, hub, dist, cnt, ovf = ix.export()
+    assert np.array_equal(off, ref.off), "label sizes differ"
+    assert np.array_equal(hub, ref.hub), "hubs differ"
+    assert np.array_equal(dist, ref.dist), "distances differ"
+    assert np.array_equal(cnt, ref.cnt), "counts differ"
+    assert np.array_equal(ovf, ref.ovf), "overflow flags differ"
+
+
+def gpu_query(ix, pairs, device=True):
+    import torch
+
+    if device:
+        d, c, f = ix.query(torch.from_numpy(pairs).cuda())
+        return d.cpu().numpy(), c.cpu().numpy(), f.cpu().numpy()
+    return ix.query(pairs)
+
+
+# --- the paper's example ---
+
+def test_paper_table(pspc):
+    g, rank, table, (s, t, sd, c) = G.load_paper_table()
+    ix = gpu_index(pspc, g, rank)
+    off, hub, dist, cnt, ovf = ix.export()
+    for v in range(10):
+        got = [(int(hub[i]), int(dist[i]), int(cnt[i])) for i in range(off[v], off[v + 1])]
+        assert got == table[v], v
+    d, cc, f = gpu_query(ix, np.array([[s, t], [t, s]], np.int32))
+    assert d.tolist() == [sd, sd] and cc.tolist() == [c, c] and f.tolist() == [0, 0]
+
+
+# --- small graphs against the oracle, across table capacities ---
+
+CAPS = [dict(), dict(cand_capacity=1024, label_capacity=1024)]
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("caps", range(len(CAPS)))
+def test_random_graphs_index_and_all_pairs(pspc, seed, caps):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 120))
+    g = G.gnp(n, float(rng.choice([0.03, 0.08, 0.2])), 300 + seed)
+    rank = G.random_rank(n, seed) if seed % 2 else G.degree_rank(g)
+    ref_ix = oracle.OracleIndex(g, rank)
+    ix = gpu_index(pspc, g, rank, **CAPS[caps])
+    assert_index_equal(ix, ref_ix.export())
+    pairs = np.array(list(itertools.product(range(n), range(n))), np.int32)
+    d, c, f = gpu_query(ix, pairs)
+    rd, rc, rf, _ = ref_ix.query(pairs)
+    assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
+
+
+@pytest.mark.parametrize("case", range(len(G.closed_forms())))
+def test_closed_forms(pspc, case):
+    g, s, t, sd, cnt = G.closed_forms()[case]
+    for rank in (G.degree_rank(g), G.random_rank(g.n, case)):
+        ix = gpu_index(pspc, g, rank)
+        assert_index_equal(ix, oracle.OracleIndex(g, rank).export())
+        d, c, f = gpu_query(ix, np.array([[s, t], [t, s], [s, s]], np.int32))
+        assert d.tolist() == [sd, sd, 0]
+        assert c.tolist() == [cnt % M64, cnt % M64, 1]
+        assert f.tolist() == [int(cnt >= M64)] * 2 + [0]
+
+
+@pytest.mark.parametrize("k", [63, 64, 65])
+def test_diamond_chain_label_overflow(pspc, k):
+    g = G.diamond_chain(k)
+    rank = np.arange(g.n, dtype=np.int32)
+    ix = gpu_index(pspc, g, rank)
+    ref = oracle.OracleIndex(g, rank).export()
+    assert_index_equal(ix, ref)
+    assert ix.stats()["overflow_entries"] == int(ref.ovf.sum())
+    assert (int(ref.ovf.sum()) > 0) == (k >= 64)
+
+
+def test_trees_isolated_components_and_tiny(pspc):
+    for g, rank in [
+        (G.random_tree(300, 1), G.random_rank(300, 1)),
+        (P.csr_from_edges(7, np.array([(0, 1), (1, 2), (4, 5)])), np.array([3, 0, 4, 6, 1, 5, 2], np.int32)),
+        (P.csr_from_edges(1, np.zeros((0, 2), np.int64)), np.array([0], np.int32)),
+        (P.csr_from_edges(5, np.zeros((0, 2), np.int64)), np.array([4, 3, 2, 1, 0], np.int32)),
+        (G.path(2), np.array([1, 0], np.int32)),
+    ]:
+        ref = oracle.OracleIndex(g, rank)
+        ix = gpu_index(pspc, g, rank)
+        assert_index_equal(ix, ref.export())
+        pairs = np.array(list(itertools.product(range(g.n), range(g.n))), np.int32).reshape(-1, 2)
+        d, c, f = gpu_query(ix, pairs)
+        rd, rc, rf, _ = ref.query(pairs)
+        assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
+
+
+# --- the named workloads that the oracle builds in seconds ---
+
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_ef16", "grid32", "grid64"])
+def test_workload_full_index(pspc, name):
+    g, rank, pairs_fn = P.workload(name)
+    ref = oracle.OracleIndex(g, rank)
+    ix = gpu_index(pspc, g, rank)
+    assert_index_equal(ix, ref.export())
+    pairs = pairs_fn(200000)
+    d, c, f = gpu_query(ix, pairs)
+    rd, rc, rf, _ = ref.query(pairs)
+    assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
+
+
+def test_ba2000_all_pairs_vs_bfs(pspc):
+    """Barabasi-Albert n=2,000, m=4: every ordered pair against BFS counting."""
+    g, rank, _ = P.workload("ba2000")
+    ix = gpu_index(pspc, g, rank)
+    n = g.n
+    pairs = np.stack([np.repeat(np.arange(n, dtype=np.int32), n), np.tile(np.arange(n, dtype=np.int32), n)], 1)
+    d, c, f = gpu_query(ix, pairs)
+    d = d.reshape(n, n)
+    c = c.reshape(n, n)
+    for s in range(n):
+        bd, bc, bf = oracle.bfs_count(g, s)
+        assert np.array_equal(d[s].astype(np.int32), np.where(bd < 0, 0xFFFF, bd)), s
+        assert np.array_equal(c[s], bc), s
+    assert not f.any()
+
+
+# --- invariance: capacities, host vs device buffers, repeated builds ---
+
+def test_layout_invariance(pspc):
+    g, rank, pairs_fn = P.workload("rmat12_ef16")
+    ref = oracle.OracleIndex(g, rank).export()
+    pairs = pairs_fn(50000)
+    outs = []
+    for kw, dev in [(dict(), True), (dict(), False), (dict(cand_capacity=1024, label_capacity=1024), True),
+                    (dict(cand_capacity=16384, label_capacity=16384), True), (dict(arena_entries=1), True)]:
+        ix = gpu_index(pspc, g, rank, device=dev, **kw)
+        assert_index_equal(ix, ref)
+        outs.append(gpu_query(ix, pairs, device=dev))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+# --- bad inputs are rejected with PSPC_E_INVAL ---
+
+def test_invalid_inputs(pspc):
+    g = G.cycle(6)
+    rank = np.arange(6, dtype=np.int32)
+    bad = []
+    bad.append((6, g.row_ptr, g.col, np.array([0, 1, 2, 3, 4, 4], np.int32)))  # not a permutation
+    bad.append((6, g.row_ptr, g.col, np.array([0, 1, 2, 3, 4, 6], np.int32)))  # out of range
+    col = g.col.copy()
+    col[0] = 0  # self loop at vertex 0
+    bad.append((6, g.row_ptr, col, rank))
+    col = g.col.copy()
+    col[0], col[1] = col[1], col[0]  # unsorted row
+    bad.append((6, g.row_ptr, col, rank))
+    asym_rp = np.array([0, 1, 3, 5], np.int64)
+    asym_col = np.array([1, 0, 2, 1, 0], np.int32)  # 2->0 without 0->2
+    bad.append((3, asym_rp, asym_col, np.arange(3, dtype=np.int32)))
+    rp = g.row_ptr.copy()
+    rp[2], rp[3] = rp[3], rp[2]  # row_ptr not monotone
+    bad.append((6, rp, g.col, rank))
+    for n, rp_, col_, rk in bad:
+        with pytest.raises(pspc.PSPCError) as ei:
+            pspc.Index.build(n, rp_, col_, rk)
+        assert ei.value.code == pspc.PSPC_E_INVAL
+    ix = gpu_index(pspc, g, rank)
+    with pytest.raises(pspc.PSPCError) as ei:
+        ix.query(np.array([[0, 6]], np.int32))
+    assert ei.value.code == pspc.PSPC_E_INVAL
+    d, c, f = ix.query(np.zeros((0, 2), np.int32))
+    assert len(d) == 0
+
+
+# --- full-size workloads: sampled outputs the oracle computes one by one ---
+
+def _check_hub_columns(ix, g, rank, hubs):
+    off, hub, dist, cnt, ovf = ix.export()
+    owner = np.repeat(np.arange(g.n), np.diff(off))
+    for w in hubs:
+        cd, cc, cf = oracle.hub_column(g, rank, int(w))
+        sel = hub == w
+        got_v = owner[sel]
+        want_v = np.flatnonzero(cd != oracle.UNREACHED)
+        assert np.array_equal(got_v, want_v), f"hub {w}: vertex set differs"
+        assert np.array_equal(dist[sel], cd[want_v]) and np.array_equal(cnt[sel], cc[want_v])
+        assert np.array_equal(ovf[sel], cf[want_v])
+    return off, hub, dist, cnt, ovf
+
+
+def _check_sampled_queries(ix, g, pairs, n_src=12):
+    d, c, f = gpu_query(ix, pairs)
+    srcs = np.unique(pairs[:, 0])[:n_src]
+    checked = 0
+    for s in srcs:
+        bd, bc, bf = oracle.bfs_count(g, int(s))
+        sel = pairs[:, 0] == s
+        t = pairs[sel, 1]
+        assert np.array_equal(d[sel].astype(np.int32), np.where(bd[t] < 0, 0xFFFF, bd[t]))
+        assert np.array_equal(c[sel], bc[t]) and np.array_equal(f[sel], bf[t])
+        checked += int(sel.sum())
+    return checked
+
+
+def test_rmat16_full_size(pspc):
+    """R-MAT scale 16, edge factor 16 (the benchmark graph): the top 100 hub
+    columns against the oracle's hub-pushing build, 40 sampled hub columns
+    against the definition, and 10^6 query pairs of which those from 12
+    sources are checked against BFS counting."""
+    g, rank, pairs_fn = P.workload("rmat16")
+    ix = gpu_index(pspc, g, rank)
+    off, hub, dist, cnt, ovf = ix.export()
+    K = 100
+    part = oracle.OracleIndex(g, rank, max_hubs=K).export()
+    keep = rank[hub] < K
+    owner = np.repeat(np.arange(g.n), np.diff(off))
+    poff = np.zeros(g.n + 1, np.int64)
+    np.cumsum(np.bincount(owner[keep], minlength=g.n), out=poff[1:])
+    assert np.array_equal(poff, part.off)
+    assert np.array_equal(hub[keep], part.hub) and np.array_equal(dist[keep], part.dist)
+    assert np.array_equal(cnt[keep], part.cnt) and np.array_equal(ovf[keep], part.ovf)
+    rng = np.random.default_rng(11)
+    _check_hub_columns(ix, g, rank, rng.choice(g.n, 40, replace=False))
+    pairs = pairs_fn(1_000_000)
+    pairs[:1000, 0] = pairs[0, 0]  # make the first source well covered
+    assert _check_sampled_queries(ix, g, pairs) >= 1000
+    st = ix.stats()
+    assert st["entries"] == len(hub)
