@@ -278,7 +278,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * K,
             "clocks": clocks}
 
-    if rank_id == 0 and world == 1:
+    if rank_id == 0 and world == 1 and args.e2e_steps > 0:
         # end to end through the public API with host buffers
         e2e_b, e2e_q = [], []
         h2d = g.row_ptr.nbytes + g.col.nbytes + rank.nbytes + pairs.nbytes
@@ -299,6 +299,7 @@ def run_ours(args):
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "queries_per_s": q / statistics.mean(e2e_q),
                        "step_s": statistics.mean(e2e_b) + statistics.mean(e2e_q)}
+    if rank_id == 0 and world == 1:
         if not args.no_cpu_baseline:
             ent, dt = cpu_baseline(g, rank)
             line["cpu_baseline"] = {

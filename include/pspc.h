@@ -64,9 +64,12 @@ typedef struct {
     int32_t cand_capacity;   /* on-chip candidate hash slots per vertex
                                 (power of two, 1024..16384; default 4096) */
     int32_t label_capacity;  /* on-chip label hash slots per vertex (power of
-                                two, 1024..16384; default 8192) */
+                                two, 1024..16384; default 8192). The two
+                                tables take 12*cand + max(6*label, 8*cand)
+                                bytes of shared memory per CTA; sizes that do
+                                not fit the device give PSPC_E_INVAL */
     int64_t arena_entries;   /* initial label arena capacity in entries
-                                (default 64 * n; grows on demand) */
+                                (default 32 * arcs + 4 * n; grows on demand) */
     int32_t max_levels;      /* stop with PSPC_E_DIST after this many levels
                                 (default 32767) */
     int32_t verbose;         /* 1: per-level line on stderr */

@@ -829,6 +829,9 @@ struct Builder {
         const uint32_t cap_c_smem = (uint32_t)o.cand_capacity;
         const uint32_t cap_u_smem = (uint32_t)o.label_capacity;
         const size_t smem_bytes = level_table_bytes(cap_c_smem, cap_u_smem);
+        int smem_optin = 0;
+        PSPC_TRY_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (smem_bytes + 1024 > (size_t)smem_optin) return PSPC_E_INVAL;  // tables must fit on chip
         PSPC_TRY_CUDA(cudaFuncSetAttribute(k_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
         int occ = 0;
         PSPC_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_level<false>, kLevelThreads, smem_bytes));

@@ -168,7 +168,7 @@ def test_layout_invariance(pspc):
     pairs = pairs_fn(50000)
     outs = []
     for kw, dev in [(dict(), True), (dict(), False), (dict(cand_capacity=1024, label_capacity=1024), True),
-                    (dict(cand_capacity=16384, label_capacity=16384), True), (dict(arena_entries=1), True)]:
+                    (dict(cand_capacity=8192, label_capacity=16384), True), (dict(arena_entries=1), True)]:
         ix = gpu_index(pspc, g, rank, device=dev, **kw)
         assert_index_equal(ix, ref)
         outs.append(gpu_query(ix, pairs, device=dev))
@@ -207,6 +207,10 @@ def test_invalid_inputs(pspc):
     assert ei.value.code == pspc.PSPC_E_INVAL
     d, c, f = ix.query(np.zeros((0, 2), np.int32))
     assert len(d) == 0
+    # on-chip tables larger than the device's shared memory are rejected
+    with pytest.raises(pspc.PSPCError) as ei:
+        pspc.Index.build(6, g.row_ptr, g.col, rank, cand_capacity=16384, label_capacity=16384)
+    assert ei.value.code == pspc.PSPC_E_INVAL
 
 
 # --- full-size workloads: sampled outputs the oracle computes one by one ---
@@ -226,8 +230,10 @@ def _check_hub_columns(ix, g, rank, hubs):
 
 
 def _check_sampled_queries(ix, g, pairs, n_src=12):
+    """Queries from pairs[0, 0] and n_src - 1 other sources against BFS."""
     d, c, f = gpu_query(ix, pairs)
-    srcs = np.unique(pairs[:, 0])[:n_src]
+    others = np.unique(pairs[:, 0])
+    srcs = [int(pairs[0, 0])] + [int(x) for x in others[:: max(1, len(others) // n_src)][: n_src - 1]]
     checked = 0
     for s in srcs:
         bd, bc, bf = oracle.bfs_count(g, int(s))
