@@ -275,6 +275,8 @@ def run_ours(args):
                          "traffic": traffic,
                          "bytes_per_step": kb / K, "kernel_ms_per_step": kms / K,
                          "launches_per_step": klaunch / K},
+            "level_kernel_ms": [round(l["kernel_ms"], 3) for l in res[-1][3]],
+            "level_ms": [round(l["ms"], 3) for l in res[-1][3]],
             "gpu_launches": launches_per_step * K,
             "clocks": clocks}
 

@@ -1,24 +1,15 @@
-// Level-synchronous pull construction of the SPC 2-hop hub-label index
-// (PSPC, arXiv 2212.00977): Theorem "Distance Dependency", Lemma
-// "Propagation", pruning rules 1 and 2, Label Merging, and Algorithm PULL.
+// pspc_build: construction of the SPC 2-hop hub-label index (PSPC, arXiv
+// 2212.00977) on one GPU -- input checks, relabelling by rank, the level
+// loop of the pull construction (Theorem "Distance Dependency": level d
+// depends only on levels < d, so levels are built one after another, each
+// fully parallel over vertices), and the final merge of each vertex's level
+// segments into one hub-sorted label (the order of Table "Shortest Path
+// Counting Labels").
 //
 // Vertices are relabelled so that id = rank (0 = highest). Level d of every
-// vertex is stored as one hub-sorted segment of a label arena (hub word with
-// the overflow flag in bit 31, uint64 count; the distance is the level).
-// Per level:
-//   k_cost      per arc u->v: how many entries of L_{d-1}(v) have a hub
-//               ranked above u (a prefix, segments are hub-sorted: rule 1);
-//               per vertex the sum (the paper's cost function) and a class.
-//   k_bucket_*  orders active vertices by decreasing cost (dynamic schedule).
-//   k_level     one CTA per vertex, persistent with a work counter: gathers
-//               the pulled entries into an on-chip hash keyed by hub, adding
-//               counts mod 2^64 with a sticky overflow flag (Label Merging);
-//               tests every candidate hub h with the distance-bounded prune
-//               query (rule 2), sorts the survivors by hub and appends them.
-// After the last non-empty level, k_finalize merges each vertex's level
-// segments into one hub-sorted label (Table "Shortest Path Counting Labels"
-// order).
-#include <cooperative_groups.h>
+// vertex is one hub-sorted segment of a label arena: a hub word (bits 0-23
+// hub, bit 31 overflow flag) and a uint64 count; the distance is the level.
+// The per-level kernels live in pspc_level.cu.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -27,36 +18,12 @@
 #include <vector>
 
 #include "pspc_internal.cuh"
-
-namespace cg = cooperative_groups;
+#include "pspc_level.cuh"
 
 namespace pspc {
 
-constexpr int kLevelThreads = 512;
-constexpr int kProbeGroup = 8;  // lanes that scan one candidate's label segment
-constexpr int kBuckets = 64;
 constexpr int kFinThreads = 256;
 constexpr int kFinSmemKeys = 8192;  // labels up to this size are merged on chip
-
-struct LevelStatus {
-    unsigned long long raw_total;
-    unsigned long long unique_total;
-    unsigned long long bump;       // arena fill after this level
-    unsigned long long need_cap_c; // largest candidate table of the off-chip class
-    unsigned long long need_cap_u; // largest label table of the off-chip class
-    unsigned long long active_arcs;
-    int n_active;
-    int n_smem;
-    int n_global;
-    int n_retry;
-    int arena_overflow;
-    int work_smem;
-    int work_global;
-    int pad;
-    int bucket_cnt[kBuckets];
-    int bucket_base[kBuckets];
-    int bucket_fill[kBuckets];
-};
 
 // ---------------------------------------------------------------------------
 // Input checks (the ABI rejects malformed graphs and orders).
@@ -134,169 +101,8 @@ __global__ void k_level0(int64_t n, uint32_t* hub_arena, uint64_t* cnt_arena, ui
     seg0[v] = seg_pack((uint64_t)v, 1u);
 }
 
-// ---------------------------------------------------------------------------
-// Per-level cost and classification.
-
-__device__ __forceinline__ uint32_t cand_cap_for(int64_t raw, int64_t u, uint32_t cap_max) {
-    const int64_t bound = raw < u ? raw : u;  // distinct hubs <= pulled entries, and < u
-    const uint64_t want = (uint64_t)(2 * bound) < 64ull ? 64ull : (uint64_t)(2 * bound);
-    return want >= cap_max ? cap_max : pow2_ceil(want);
-}
-__device__ __forceinline__ uint32_t label_cap_for(int64_t lab) {
-    const uint64_t want = (uint64_t)(lab + lab / 3 + 1);
-    return pow2_ceil(want < 64ull ? 64ull : want);
-}
-
-// Warp per vertex u: updates |L_<d(u)| with level d-1, and for every arc
-// u->v counts the entries of L_{d-1}(v) whose hub ranks above u.
-__global__ void k_cost(int d, int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                       const uint64_t* __restrict__ seg_prev, const uint32_t* __restrict__ hub_arena,
-                       uint32_t* __restrict__ cnt_arc, int64_t* __restrict__ raw_u, int64_t* __restrict__ lab_size,
-                       LevelStatus* stt, uint32_t cap_u_smem, int32_t* __restrict__ glist) {
-    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (u >= n) return;
-    int64_t raw = 0;
-    for (int64_t a = rp[u] + lane; a < rp[u + 1]; a += 32) {
-        const int32_t v = col[a];
-        const uint64_t s = seg_prev[v];
-        const uint32_t* h = hub_arena + seg_start(s);
-        uint32_t lo = 0, hi = seg_len(s);
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if ((__ldg(h + mid) & kHubMask) < (uint32_t)u) lo = mid + 1; else hi = mid;
-        }
-        cnt_arc[a] = lo;
-        raw += lo;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xFFFFFFFFu, raw, o);
-    if (lane != 0) return;
-    const int64_t ls = lab_size[u] + seg_len(seg_prev[u]);
-    lab_size[u] = ls;
-    raw_u[u] = raw;
-    if (raw == 0) return;
-    atomicAdd(&stt->raw_total, (unsigned long long)raw);
-    atomicAdd(&stt->active_arcs, (unsigned long long)(rp[u + 1] - rp[u]));
-    atomicAdd(&stt->n_active, 1);
-    if (label_cap_for(ls) <= cap_u_smem) {
-        atomicAdd(&stt->n_smem, 1);
-        atomicAdd(&stt->bucket_cnt[63 - __clzll((unsigned long long)raw)], 1);
-    } else {
-        const int p = atomicAdd(&stt->n_global, 1);
-        glist[p] = (int32_t)u;
-        const uint64_t cu = label_cap_for(ls);
-        const uint64_t cc = cand_cap_for(raw, u, 1u << 30);
-        atomicMax(&stt->need_cap_u, (unsigned long long)cu);
-        atomicMax(&stt->need_cap_c, (unsigned long long)cc);
-    }
-}
-
-__global__ void k_bucket_base(LevelStatus* stt) {
-    if (threadIdx.x != 0) return;
-    int run = 0;
-    for (int b = kBuckets - 1; b >= 0; --b) {  // most expensive vertices first
-        stt->bucket_base[b] = run;
-        run += stt->bucket_cnt[b];
-        stt->bucket_fill[b] = 0;
-    }
-}
-
-__global__ void k_bucket_fill(int64_t n, const int64_t* __restrict__ raw_u, const int64_t* __restrict__ lab_size,
-                              LevelStatus* stt, uint32_t cap_u_smem, int32_t* __restrict__ items) {
-    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    const int64_t raw = raw_u[u];
-    if (raw == 0 || label_cap_for(lab_size[u]) > cap_u_smem) return;
-    const int b = 63 - __clzll((unsigned long long)raw);
-    items[stt->bucket_base[b] + atomicAdd(&stt->bucket_fill[b], 1)] = (int32_t)u;
-}
-
-// ---------------------------------------------------------------------------
-// The level kernel.
-
-struct LevelArgs {
-    int d;
-    int64_t n;
-    const int64_t* rp;
-    const int32_t* col;
-    const uint32_t* cnt_arc;
-    const uint64_t* seg;  // [levels][n]
-    uint64_t* seg_out;    // row d
-    uint32_t* hub_arena;
-    uint64_t* cnt_arena;
-    unsigned long long arena_cap;
-    const int64_t* raw_u;
-    const int64_t* lab_size;
-    const int32_t* items;
-    int n_items;
-    int* work;
-    LevelStatus* stt;
-    int32_t* retry_list;  // appended at retry_list[n_global + k]
-    uint32_t cap_c_max;   // candidate table slots (on chip, or per-CTA scratch)
-    uint32_t cap_u_max;   // label table slots
-    uint8_t* gscratch;    // per-CTA table memory when tables are off chip
-    size_t gscratch_stride;
-};
-
-__host__ __device__ inline size_t table_region_bytes(uint32_t cap_c, uint32_t cap_u) {
-    const size_t a = (size_t)cap_u * 6, b = (size_t)cap_c * 8;
-    return a > b ? a : b;
-}
-
-__host__ __device__ inline size_t level_table_bytes(uint32_t cap_c, uint32_t cap_u) {
-    const size_t region = table_region_bytes(cap_c, cap_u);
-    return (size_t)cap_c * 8 + ((region + 15) & ~(size_t)15) + (size_t)cap_c * 4;
-}
-
-__device__ __forceinline__ bool cand_insert(uint32_t* keys, unsigned long long* cnts, uint32_t cap, uint32_t limit,
-                                            uint32_t h, uint64_t c, uint32_t ovf, int* nkeys, volatile int* abort_flag) {
-    uint32_t slot = hash_hub(h) & (cap - 1);
-    for (uint32_t probe = 0; probe < cap; ++probe) {
-        uint32_t k = ((volatile uint32_t*)keys)[slot];
-        if (k == kEmpty) {
-            if (*abort_flag) return false;
-            k = atomicCAS(&keys[slot], kEmpty, h);
-            if (k == kEmpty) {
-                if ((uint32_t)(atomicAdd(nkeys, 1) + 1) > limit) *abort_flag = 1;
-                k = h;
-            }
-        }
-        if ((k & kHubMask) == h) {
-            const unsigned long long old = atomicAdd(&cnts[slot], (unsigned long long)c);
-            if (ovf | (old + c < old)) atomicOr(&keys[slot], kOvfBit);
-            return true;
-        }
-        slot = (slot + 1) & (cap - 1);
-    }
-    *abort_flag = 1;
-    return false;
-}
-
-__device__ __forceinline__ void label_insert(uint32_t* keys, uint16_t* lvl, uint32_t cap, uint32_t x, uint16_t l) {
-    uint32_t slot = hash_hub(x) & (cap - 1);
-    for (uint32_t probe = 0; probe < cap; ++probe) {
-        const uint32_t k = atomicCAS(&keys[slot], kEmpty, x);
-        if (k == kEmpty || k == x) {
-            lvl[slot] = l;
-            return;
-        }
-        slot = (slot + 1) & (cap - 1);
-    }
-}
-
-__device__ __forceinline__ uint32_t label_lookup(const uint32_t* keys, const uint16_t* lvl, uint32_t cap, uint32_t x) {
-    uint32_t slot = hash_hub(x) & (cap - 1);
-    for (uint32_t probe = 0; probe < cap; ++probe) {
-        const uint32_t k = keys[slot];
-        if (k == x) return lvl[slot];
-        if (k == kEmpty) return 0xFFFFu;
-        slot = (slot + 1) & (cap - 1);
-    }
-    return 0xFFFFu;
-}
-
-__device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
+// Bitonic sort of buf[0..P) (P a power of two) by the whole block.
+__device__ void fin_bitonic_sort(unsigned long long* buf, uint32_t P) {
     for (uint32_t k = 2; k <= P; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
             for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
@@ -311,157 +117,6 @@ __device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
             }
             __syncthreads();
         }
-    }
-}
-
-template <bool kOffChip>
-__global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_item, s_nkeys, s_abort, s_nsurv, s_pos;
-    __shared__ unsigned long long s_base;
-
-    uint8_t* tables = kOffChip ? A.gscratch + (size_t)blockIdx.x * A.gscratch_stride : smem;
-    unsigned long long* ccnt = (unsigned long long*)tables;
-    const size_t region = table_region_bytes(A.cap_c_max, A.cap_u_max);
-    uint8_t* reg = tables + (size_t)A.cap_c_max * 8;
-    uint32_t* ukeys = (uint32_t*)reg;
-    unsigned long long* sortbuf = (unsigned long long*)reg;
-    uint32_t* ckeys = (uint32_t*)(reg + ((region + 15) & ~(size_t)15));
-
-    const int tid = threadIdx.x;
-    const int d = A.d;
-    const int64_t n = A.n;
-    auto tile = cg::tiled_partition<kProbeGroup>(cg::this_thread_block());
-    const int group = tile.meta_group_rank();
-    const int ngroups = kLevelThreads / kProbeGroup;
-    const int warp = tid >> 5, lane = tid & 31;
-
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(A.work, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= A.n_items) break;
-        const int64_t u = A.items[item];
-        const int64_t raw = A.raw_u[u];
-        const int64_t lab = A.lab_size[u];
-        const uint32_t cap_u = label_cap_for(lab);
-        const uint32_t cap_c = cand_cap_for(raw, u, A.cap_c_max);
-        // Off chip the table is sized for every distinct hub; on chip a
-        // vertex whose candidates overflow is handed to the off-chip pass.
-        const uint32_t limit = (kOffChip || cap_c < A.cap_c_max) ? cap_c : cap_c - kLevelThreads - 64;
-        uint16_t* ulvl = (uint16_t*)(reg + (size_t)cap_u * 4);
-
-        for (uint32_t i = tid; i < cap_c; i += kLevelThreads) {
-            ckeys[i] = kEmpty;
-            ccnt[i] = 0ull;
-        }
-        for (uint32_t i = tid; i < cap_u; i += kLevelThreads) ukeys[i] = kEmpty;
-        if (tid == 0) {
-            s_nkeys = 0;
-            s_abort = 0;
-            s_nsurv = 0;
-            s_pos = 0;
-        }
-        __syncthreads();
-
-        // L_<d(u) as hub -> level (levels 0..d-1).
-        for (int l = 0; l < d; ++l) {
-            const uint64_t s = __ldg(A.seg + (int64_t)l * n + u);
-            const uint32_t len = seg_len(s);
-            const uint32_t* hs = A.hub_arena + seg_start(s);
-            for (uint32_t i = tid; i < len; i += kLevelThreads)
-                label_insert(ukeys, ulvl, cap_u, __ldg(hs + i) & kHubMask, (uint16_t)l);
-        }
-
-        // Pull: entries of L_{d-1}(v), v in N(u), with hub above u (a prefix),
-        // merged per hub.
-        {
-            const int64_t a0 = A.rp[u], a1 = A.rp[u + 1];
-            const uint64_t* segp = A.seg + (int64_t)(d - 1) * n;
-            for (int64_t a = a0 + warp; a < a1; a += kLevelThreads / 32) {
-                if (*(volatile int*)&s_abort) break;
-                const uint32_t c = __ldg(A.cnt_arc + a);
-                if (c == 0) continue;
-                const uint64_t s = __ldg(segp + __ldg(A.col + a));
-                const uint64_t st = seg_start(s);
-                for (uint32_t i = lane; i < c; i += 32) {
-                    const uint32_t hw = __ldg(A.hub_arena + st + i);
-                    const uint64_t cc = __ldg((const unsigned long long*)A.cnt_arena + st + i);
-                    if (!cand_insert(ckeys, ccnt, cap_c, limit, hw & kHubMask, cc, hw >> 31, &s_nkeys, &s_abort))
-                        break;
-                }
-            }
-        }
-        __syncthreads();
-        if (s_abort) {
-            if (tid == 0) {
-                const int p = atomicAdd(&A.stt->n_retry, 1);
-                A.retry_list[p] = (int32_t)u;
-                atomicMax(&A.stt->need_cap_c, (unsigned long long)cand_cap_for(raw, u, 1u << 30));
-                atomicMax(&A.stt->need_cap_u, (unsigned long long)cap_u);
-            }
-            __syncthreads();
-            continue;
-        }
-
-        // Prune rule 2, distance-bounded: a hub x of L_k(h) (k <= d-2) is a
-        // witness iff x in L(u) at level <= d-1-k; k = 0 is x = h itself.
-        for (uint32_t slot = group; slot < cap_c; slot += ngroups) {
-            const uint32_t key = ckeys[slot];
-            if (key == kEmpty) continue;
-            const uint32_t h = key & kHubMask;
-            bool pruned = label_lookup(ukeys, ulvl, cap_u, h) != 0xFFFFu;
-            for (int k = 1; k <= d - 2 && !pruned; ++k) {
-                const uint64_t s = __ldg(A.seg + (int64_t)k * n + h);
-                const uint32_t len = seg_len(s);
-                const uint32_t* xs = A.hub_arena + seg_start(s);
-                const uint32_t thr = (uint32_t)(d - 1 - k);
-                for (uint32_t b = 0; b < len && !pruned; b += kProbeGroup) {
-                    const uint32_t i = b + tile.thread_rank();
-                    bool hit = false;
-                    if (i < len) hit = label_lookup(ukeys, ulvl, cap_u, __ldg(xs + i) & kHubMask) <= thr;
-                    pruned = tile.any(hit);
-                }
-            }
-            if (!pruned && tile.thread_rank() == 0) {
-                ckeys[slot] = key | kMarkBit;
-                atomicAdd(&s_nsurv, 1);
-            }
-        }
-        __syncthreads();
-
-        const int S = s_nsurv;
-        if (S > 0) {
-            const uint32_t P = pow2_ceil((uint64_t)S);
-            for (uint32_t slot = tid; slot < cap_c; slot += kLevelThreads) {
-                const uint32_t key = ckeys[slot];
-                if (key != kEmpty && (key & kMarkBit)) {
-                    const int p = atomicAdd(&s_pos, 1);
-                    sortbuf[p] = ((unsigned long long)(key & kHubMask) << 32) | slot;
-                }
-            }
-            for (uint32_t i = S + tid; i < P; i += kLevelThreads) sortbuf[i] = ~0ull;
-            __syncthreads();
-            block_bitonic_sort(sortbuf, P);
-            if (tid == 0) {
-                const unsigned long long base = atomicAdd(&A.stt->bump, (unsigned long long)S);
-                if (base + S > A.arena_cap) atomicOr(&A.stt->arena_overflow, 1);
-                s_base = base;
-            }
-            __syncthreads();
-            const unsigned long long base = s_base;
-            if (base + S <= A.arena_cap) {
-                for (int i = tid; i < S; i += kLevelThreads) {
-                    const uint32_t slot = (uint32_t)sortbuf[i];
-                    const uint32_t key = ckeys[slot];
-                    A.hub_arena[base + i] = (key & kHubMask) | (key & kOvfBit);
-                    A.cnt_arena[base + i] = ccnt[slot];
-                }
-                if (tid == 0) A.seg_out[u] = seg_pack(base, (uint32_t)S);
-            }
-        }
-        if (tid == 0) atomicAdd(&A.stt->unique_total, (unsigned long long)s_nkeys);
-        __syncthreads();
     }
 }
 
@@ -534,7 +189,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinArgs F) {
         const uint32_t P = pow2_ceil((uint64_t)T);
         for (uint32_t i = (uint32_t)T + tid; i < P; i += kFinThreads) keys[i] = ~0ull;
         __syncthreads();
-        block_bitonic_sort(keys, P);
+        fin_bitonic_sort(keys, P);
         unsigned long long novf = 0;
         for (int64_t i = tid; i < T; i += kFinThreads) {
             const unsigned long long k = keys[i];
@@ -570,6 +225,14 @@ static void dfree(T*& p, cudaStream_t st) {
     p = nullptr;
 }
 
+struct LevelPlan {
+    int map_kind = kMapBitmap;
+    uint32_t cap_c = 0, cap_u = 0, bm_words = 0;
+    int64_t label_limit = 0;
+    size_t smem_bytes = 0;
+    int occupancy = 0;
+};
+
 struct Builder {
     cudaStream_t st;
     int dev = 0, sms = 0;
@@ -593,6 +256,7 @@ struct Builder {
     uint64_t* seg = nullptr;
     int seg_levels_cap = 0;
     uint32_t* cnt_arc = nullptr;
+    int32_t* arc_src = nullptr;
     int64_t* raw_u = nullptr;
     int64_t* lab_size = nullptr;
     int32_t* items = nullptr;
@@ -606,6 +270,7 @@ struct Builder {
     Index out;
     cudaEvent_t ek0 = nullptr, ek1 = nullptr;
     float kernel_ms = 0.f;  // level-kernel time of the current level
+    int smem_optin = 0;
 
     ~Builder() {
         dfree(rp_in, st);
@@ -618,6 +283,7 @@ struct Builder {
         dfree(cnt_arena, st);
         dfree(seg, st);
         dfree(cnt_arc, st);
+        dfree(arc_src, st);
         dfree(raw_u, st);
         dfree(lab_size, st);
         dfree(items, st);
@@ -755,8 +421,10 @@ struct Builder {
         return PSPC_OK;
     }
 
-    int run_level_kernels(int d, uint32_t cap_c_smem, uint32_t cap_u_smem, size_t smem_bytes, int occ_smem,
-                          int& n_offchip) {
+    // Launches the on-chip level kernel over the bucketed vertices, then the
+    // off-chip variant over the vertices whose labels or candidates do not
+    // fit on chip. Reads the level status after each.
+    int run_level_kernels(int d, const LevelPlan& plan, int& n_offchip) {
         LevelArgs A;
         memset(&A, 0, sizeof(A));
         A.d = d;
@@ -777,14 +445,15 @@ struct Builder {
             A.items = items;
             A.n_items = hstt->n_smem;
             A.work = &stt->work_smem;
-            A.cap_c_max = cap_c_smem;
-            A.cap_u_max = cap_u_smem;
-            const int grid = std::min(hstt->n_smem, sms * occ_smem);
+            A.cap_c_max = plan.cap_c;
+            A.cap_u_max = plan.cap_u;
+            A.bm_words = plan.bm_words;
+            const int grid = std::min(hstt->n_smem, sms * plan.occupancy);
             cudaEventRecord(ek0, st);
-            k_level<false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
+            cudaError_t e = launch_level(plan.map_kind, false, grid, plan.smem_bytes, A, st);
             cudaEventRecord(ek1, st);
             out.launches += 1;
-            PSPC_TRY_CUDA(cudaGetLastError());
+            PSPC_TRY_CUDA(e);
         }
         int rc = read_status();
         if (rc) return rc;
@@ -798,7 +467,7 @@ struct Builder {
         if (n_off > 0) {
             const uint32_t cc = (uint32_t)std::max<unsigned long long>(hstt->need_cap_c, 64);
             const uint32_t cu = (uint32_t)std::max<unsigned long long>(hstt->need_cap_u, 64);
-            const size_t stride = (level_table_bytes(cc, cu) + 255) & ~(size_t)255;
+            const size_t stride = (level_layout(cc, hashmap_bytes(cu)).total + 255) & ~(size_t)255;
             const size_t budget = (size_t)4 << 30;
             int grid = (int)std::min<size_t>((size_t)n_off, std::max<size_t>(1, budget / stride));
             grid = std::min(grid, sms * 2);
@@ -812,10 +481,10 @@ struct Builder {
             A.gscratch = gscratch;
             A.gscratch_stride = stride;
             cudaEventRecord(ek0, st);
-            k_level<true><<<grid, kLevelThreads, 0, st>>>(A);
+            cudaError_t e = launch_level(kMapHash, true, grid, 0, A, st);
             cudaEventRecord(ek1, st);
             out.launches += 1;
-            PSPC_TRY_CUDA(cudaGetLastError());
+            PSPC_TRY_CUDA(e);
             rc = read_status();
             if (rc) return rc;
             float ms = 0.f;
@@ -825,25 +494,47 @@ struct Builder {
         return PSPC_OK;
     }
 
-    int build_levels() {
-        const uint32_t cap_c_smem = (uint32_t)o.cand_capacity;
-        const uint32_t cap_u_smem = (uint32_t)o.label_capacity;
-        const size_t smem_bytes = level_table_bytes(cap_c_smem, cap_u_smem);
-        int smem_optin = 0;
-        PSPC_TRY_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        if (smem_bytes + 1024 > (size_t)smem_optin) return PSPC_E_INVAL;  // tables must fit on chip
-        PSPC_TRY_CUDA(cudaFuncSetAttribute(k_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
-        int occ = 0;
-        PSPC_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_level<false>, kLevelThreads, smem_bytes));
-        if (occ < 1) return PSPC_E_INVAL;
+    // How level d runs on chip: level bitmaps when (d-1) bitmaps of n bits
+    // fit the bitmap budget, else a label hash of cap_u slots (labels that
+    // need more go off chip).
+    int plan_level(int d, LevelPlan& plan) {
+        plan.cap_c = (uint32_t)o.cand_capacity;
+        plan.cap_u = (uint32_t)o.label_capacity;
+        plan.bm_words = (uint32_t)((n + 31) / 32);
+        size_t map_bytes;
+        if (bitmap_bytes(d, plan.bm_words) <= kBitmapBudget) {
+            plan.map_kind = kMapBitmap;
+            plan.label_limit = INT64_MAX;
+            map_bytes = bitmap_bytes(d, plan.bm_words);
+        } else {
+            plan.map_kind = kMapHash;
+            int64_t lo = 0, hi = plan.cap_u;  // largest label size whose hash fits cap_u slots
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) / 2;
+                if (label_cap_for(mid) <= plan.cap_u) lo = mid; else hi = mid - 1;
+            }
+            plan.label_limit = lo;
+            map_bytes = hashmap_bytes(plan.cap_u);
+        }
+        plan.smem_bytes = level_layout(plan.cap_c, map_bytes).total;
+        if (plan.smem_bytes + 1024 > (size_t)smem_optin) return PSPC_E_INVAL;  // tables must fit on chip
+        PSPC_TRY_CUDA(level_kernel_attrs(plan.map_kind, plan.smem_bytes, &plan.occupancy));
+        if (plan.occupancy < 1) return PSPC_E_INVAL;
+        return PSPC_OK;
+    }
 
-        int rc = ensure_seg_levels(16);
+    int build_levels() {
+        PSPC_TRY_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        LevelPlan plan;
+        int rc = plan_level(1, plan);  // rejects option sizes that cannot run at all
         if (rc) return rc;
+        if ((rc = ensure_seg_levels(16))) return rc;
         const unsigned long long cap0 = o.arena_entries > 0 ? (unsigned long long)o.arena_entries
                                                             : (unsigned long long)(32 * arcs + 4 * n);
         rc = grow_arena(std::max<unsigned long long>(cap0, (unsigned long long)n + 1024), 0);
         if (rc) return rc;
         PSPC_TRY_CUDA(dalloc(&cnt_arc, arcs, st));
+        PSPC_TRY_CUDA(dalloc(&arc_src, arcs, st));
         PSPC_TRY_CUDA(dalloc(&raw_u, n, st));
         PSPC_TRY_CUDA(dalloc(&lab_size, n, st));
         PSPC_TRY_CUDA(dalloc(&items, n, st));
@@ -851,6 +542,8 @@ struct Builder {
         PSPC_TRY_CUDA(dalloc(&stt, 1, st));
         PSPC_TRY_CUDA(cudaMallocHost((void**)&hstt, sizeof(LevelStatus)));
         PSPC_TRY_CUDA(cudaMemsetAsync(lab_size, 0, n * 8, st));
+        PSPC_TRY_CUDA(launch_arc_src(rp_r, n, arc_src, st));
+        out.launches += 1;
 
         k_level0<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, hub_arena, cnt_arena, seg);
         out.launches += 1;
@@ -869,17 +562,15 @@ struct Builder {
                 break;
             }
             if ((rc = ensure_seg_levels(d + 1))) break;
+            if ((rc = plan_level(d, plan))) break;
             cudaEventRecord(e0, st);
             cudaMemsetAsync(seg + (int64_t)d * n, 0, n * 8, st);
             cudaMemsetAsync(stt, 0, sizeof(LevelStatus), st);
             cudaMemcpyAsync(&stt->bump, &lvl_base[d], 8, cudaMemcpyHostToDevice, st);
-            k_cost<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(d, n, rp_r, col_r, seg + (int64_t)(d - 1) * n,
-                                                                       hub_arena, cnt_arc, raw_u, lab_size, stt,
-                                                                       cap_u_smem, glist);
-            k_bucket_base<<<1, 32, 0, st>>>(stt);
-            k_bucket_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, raw_u, lab_size, stt, cap_u_smem, items);
-            out.launches += 3;
-            if ((rc = cuda_status(cudaGetLastError()))) break;
+            cudaError_t ce = launch_cost(d, n, arcs, rp_r, col_r, arc_src, seg + (int64_t)(d - 1) * n, hub_arena,
+                                         cnt_arc, raw_u, lab_size, stt, plan.label_limit, glist, items, st,
+                                         &out.launches);
+            if ((rc = cuda_status(ce))) break;
             if ((rc = read_status())) break;
             if (hstt->n_active == 0) break;
             const long long raw_total = (long long)hstt->raw_total;
@@ -887,7 +578,7 @@ struct Builder {
             int n_off = 0;
             kernel_ms = 0.f;
             for (int attempt = 0;; ++attempt) {
-                if ((rc = run_level_kernels(d, cap_c_smem, cap_u_smem, smem_bytes, occ, n_off))) break;
+                if ((rc = run_level_kernels(d, plan, n_off))) break;
                 if (!hstt->arena_overflow) break;
                 kernel_ms = 0.f;
                 if (attempt > 4) {

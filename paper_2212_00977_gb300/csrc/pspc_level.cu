@@ -1,0 +1,507 @@
+// One distance level d of the pull construction (Algorithm PULL; Theorem
+// "Distance Dependency"; Lemma "Propagation"; pruning rules 1 and 2; Label
+// Elimination and Label Merging; cost-function schedule).
+//
+// k_cost_arcs / k_cost_vertices
+//   For every arc u->v: how many entries of L_{d-1}(v) have a hub ranked
+//   above u. Level segments are hub-sorted, so rule 1 keeps a prefix, found
+//   by binary search. Per vertex the sum is the pulled-entry count (the
+//   paper's cost function); active vertices are bucketed by it so that the
+//   most expensive ones start first.
+//
+// k_level  (one CTA per vertex, persistent CTAs taking vertices in bucket
+//   order from a work counter)
+//   1. The label map of u: which hubs x are in L_<d(u), and at which
+//      distance. Cumulative bitmaps B_j = {x : d_u(x) <= j}, j = 1..d-1,
+//      when they fit on chip; otherwise an open-addressing hash x -> d_u(x).
+//   2. Pull: the arcs of u are staged in chunks, their pulled-entry counts
+//      prefix-summed, and the flattened entries split evenly over the
+//      warps. An entry (h, d-1, c) whose hub h is already in L_<d(u) is
+//      dropped before its count is read: then Query(h, u) <= d_u(h) < d,
+//      so rule 2 would prune it (Label Elimination at no cost). The others
+//      are merged per hub in an on-chip hash (count += c mod 2^64; the
+//      overflow flag takes the entry's flag and the carry: Label Merging).
+//   3. Prune (rule 2) for every merged candidate h. A common hub x of
+//      L_<d(u) and L_<d(h) with d_u(x) + d_h(x) < d exists iff some
+//      x in L_k(h), 1 <= k <= d-2, has d_u(x) <= d-1-k (the case k = 0,
+//      x = h, was handled in step 2; entries of h at distance d-1 cannot
+//      help because d_u(x) >= 1 for x != u). Groups of 8 lanes scan these
+//      segments with early exit, taking candidates from a shared counter.
+//   4. Survivors are sorted by hub (bitonic, on chip) and appended to the
+//      label arena as L_d(u); the arena slot comes from one atomic add.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "pspc_level.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pspc {
+
+constexpr int kProbeGroup = 8;   // lanes per candidate in the prune scan
+constexpr int kProbeUnroll = 4;  // loads in flight per lane in the prune scan
+constexpr int kGatherUnroll = 4; // loads in flight per lane in the pull
+constexpr uint32_t kPrunedBit = 0x80000000u;
+
+// ---------------------------------------------------------------------------
+// Cost (rule 1 prefix per arc) and classification.
+
+__global__ void k_arc_src(const int64_t* __restrict__ rp, int64_t n, int32_t* __restrict__ arc_src) {
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= n) return;
+    for (int64_t a = rp[u] + lane; a < rp[u + 1]; a += 32) arc_src[a] = (int32_t)u;
+}
+
+__global__ void k_cost_arcs(int64_t arcs, const int32_t* __restrict__ arc_src, const int32_t* __restrict__ col,
+                            const uint64_t* __restrict__ seg_prev, const uint32_t* __restrict__ hub_arena,
+                            uint32_t* __restrict__ cnt_arc, unsigned long long* __restrict__ raw_u) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= arcs) return;
+    const uint32_t u = (uint32_t)arc_src[a];
+    const uint64_t s = __ldg(seg_prev + col[a]);
+    const uint32_t* h = hub_arena + seg_start(s);
+    uint32_t lo = 0, hi = seg_len(s);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((__ldg(h + mid) & kHubMask) < u) lo = mid + 1; else hi = mid;
+    }
+    cnt_arc[a] = lo;
+    if (lo) atomicAdd(raw_u + u, (unsigned long long)lo);
+}
+
+__global__ void k_cost_vertices(int64_t n, const int64_t* __restrict__ rp, const uint64_t* __restrict__ seg_prev,
+                                const int64_t* __restrict__ raw_u, int64_t* __restrict__ lab_size, LevelStatus* stt,
+                                int64_t label_limit, int32_t* __restrict__ glist) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int64_t ls = lab_size[u] + seg_len(seg_prev[u]);
+    lab_size[u] = ls;
+    const int64_t raw = raw_u[u];
+    if (raw == 0) return;
+    atomicAdd(&stt->raw_total, (unsigned long long)raw);
+    atomicAdd(&stt->active_arcs, (unsigned long long)(rp[u + 1] - rp[u]));
+    atomicAdd(&stt->n_active, 1);
+    if (ls <= label_limit) {
+        atomicAdd(&stt->n_smem, 1);
+        atomicAdd(&stt->bucket_cnt[63 - __clzll((unsigned long long)raw)], 1);
+    } else {
+        const int p = atomicAdd(&stt->n_global, 1);
+        glist[p] = (int32_t)u;
+        atomicMax(&stt->need_cap_u, (unsigned long long)label_cap_for(ls));
+        atomicMax(&stt->need_cap_c, (unsigned long long)cand_cap_for(raw, u, 1u << 30));
+    }
+}
+
+__global__ void k_bucket_base(LevelStatus* stt) {
+    if (threadIdx.x != 0) return;
+    int run = 0;
+    for (int b = kBuckets - 1; b >= 0; --b) {  // most expensive vertices first
+        stt->bucket_base[b] = run;
+        run += stt->bucket_cnt[b];
+        stt->bucket_fill[b] = 0;
+    }
+}
+
+__global__ void k_bucket_fill(int64_t n, const int64_t* __restrict__ raw_u, const int64_t* __restrict__ lab_size,
+                              LevelStatus* stt, int64_t label_limit, int32_t* __restrict__ items) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int64_t raw = raw_u[u];
+    if (raw == 0 || lab_size[u] > label_limit) return;
+    const int b = 63 - __clzll((unsigned long long)raw);
+    items[stt->bucket_base[b] + atomicAdd(&stt->bucket_fill[b], 1)] = (int32_t)u;
+}
+
+// ---------------------------------------------------------------------------
+// Label maps of L_<d(u).
+
+struct BitMap {
+    uint32_t* bits;  // (d-1) bitmaps of `words` words; bitmap j-1 = {x : d_u(x) <= j}
+    uint32_t words;
+    int d;
+    __device__ void clear() const {
+        const uint32_t total = (uint32_t)(d - 1) * words;
+        for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) bits[i] = 0u;
+    }
+    __device__ void insert(uint32_t x, int l) const {
+        if (l == 0) return;  // u itself is never a candidate or a witness
+        const uint32_t m = 1u << (x & 31);
+        for (int j = l; j <= d - 1; ++j) atomicOr(&bits[(uint32_t)(j - 1) * words + (x >> 5)], m);
+    }
+    __device__ bool within(uint32_t x, int thr) const {  // d_u(x) <= thr, 1 <= thr <= d-1
+        return (bits[(uint32_t)(thr - 1) * words + (x >> 5)] >> (x & 31)) & 1u;
+    }
+    __device__ bool member(uint32_t x) const { return d > 1 && within(x, d - 1); }
+};
+
+struct HashMap {
+    uint32_t* keys;
+    uint16_t* lvl;
+    uint32_t cap;
+    __device__ void clear() const {
+        for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) keys[i] = kEmpty;
+    }
+    __device__ void insert(uint32_t x, int l) const {
+        uint32_t slot = hash_hub(x) & (cap - 1);
+        for (uint32_t probe = 0; probe < cap; ++probe) {
+            const uint32_t k = atomicCAS(&keys[slot], kEmpty, x);
+            if (k == kEmpty || k == x) {
+                lvl[slot] = (uint16_t)l;
+                return;
+            }
+            slot = (slot + 1) & (cap - 1);
+        }
+    }
+    __device__ uint32_t lookup(uint32_t x) const {
+        uint32_t slot = hash_hub(x) & (cap - 1);
+        for (uint32_t probe = 0; probe < cap; ++probe) {
+            const uint32_t k = keys[slot];
+            if (k == x) return lvl[slot];
+            if (k == kEmpty) return 0xFFFFu;
+            slot = (slot + 1) & (cap - 1);
+        }
+        return 0xFFFFu;
+    }
+    __device__ bool within(uint32_t x, int thr) const { return lookup(x) <= (uint32_t)thr; }
+    __device__ bool member(uint32_t x) const { return lookup(x) != 0xFFFFu; }
+};
+
+// ---------------------------------------------------------------------------
+// Block helpers.
+
+__device__ __forceinline__ bool cand_insert(uint32_t* keys, unsigned long long* cnts, uint32_t cap, uint32_t limit,
+                                            uint32_t h, uint64_t c, uint32_t ovf, int* nkeys, int* abort_flag) {
+    uint32_t slot = hash_hub(h) & (cap - 1);
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        uint32_t k = ((volatile uint32_t*)keys)[slot];
+        if (k == kEmpty) {
+            if (*(volatile int*)abort_flag) return false;
+            k = atomicCAS(&keys[slot], kEmpty, h);
+            if (k == kEmpty) {
+                if ((uint32_t)(atomicAdd(nkeys, 1) + 1) > limit) *(volatile int*)abort_flag = 1;
+                k = h;
+            }
+        }
+        if ((k & kHubMask) == h) {
+            const unsigned long long old = atomicAdd(&cnts[slot], (unsigned long long)c);
+            if (ovf | (old + c < old)) atomicOr(&keys[slot], kOvfBit);
+            return true;
+        }
+        slot = (slot + 1) & (cap - 1);
+    }
+    *(volatile int*)abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ long long warp_incl_scan64(long long v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of a[0..n) (n <= blockDim.x) in place; a[n] = total.
+__device__ long long block_excl_scan(long long* a, int n, long long* wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const long long v = tid < n ? a[tid] : 0;
+    const long long incl = warp_incl_scan64(v);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        long long t = lane < nw ? wsum[lane] : 0;
+        t = warp_incl_scan64(t);
+        if (lane < nw) wsum[lane] = t;
+    }
+    __syncthreads();
+    const long long total = wsum[nw - 1];
+    if (tid < n) a[tid] = incl - v + (warp ? wsum[warp - 1] : 0);
+    if (tid == 0) a[n] = total;
+    __syncthreads();
+    return total;
+}
+
+__device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = buf[i], b = buf[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        buf[i] = b;
+                        buf[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The level kernel.
+
+template <int kMap, bool kOffChip>
+__global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int s_item, s_nkeys, s_abort, s_m, s_next, s_nsurv;
+    __shared__ unsigned long long s_base;
+    __shared__ long long s_wsum[kLevelThreads / 32];
+
+    const int d = A.d;
+    const int64_t n = A.n;
+    const size_t map_bytes = kMap == kMapBitmap ? bitmap_bytes(d, A.bm_words) : hashmap_bytes(A.cap_u_max);
+    const LevelLayout L = level_layout(A.cap_c_max, map_bytes);
+    uint8_t* base = kOffChip ? A.gscratch + (size_t)blockIdx.x * A.gscratch_stride : smem;
+    unsigned long long* ccnt = (unsigned long long*)(base + L.cnt);
+    uint32_t* ckeys = (uint32_t*)(base + L.key);
+    uint8_t* mapr = base + L.map;
+    unsigned long long* sortbuf = (unsigned long long*)mapr;
+    uint32_t* list = (uint32_t*)(base + L.list);
+    uint64_t* st = (uint64_t*)(base + L.st);
+    long long* pfx = (long long*)(base + L.pfx);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kLevelThreads / 32;
+    auto tile = cg::tiled_partition<kProbeGroup>(cg::this_thread_block());
+    const int glane = tile.thread_rank();
+    const uint64_t* seg_prev = A.seg + (int64_t)(d - 1) * n;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= A.n_items) break;
+        const int64_t u = A.items[item];
+        const int64_t raw = A.raw_u[u];
+        const uint32_t cap_c = cand_cap_for(raw, u, A.cap_c_max);
+        // Off chip the table holds every distinct hub; on chip a vertex whose
+        // candidates overflow is handed to the off-chip pass.
+        const uint32_t limit = (kOffChip || cap_c < A.cap_c_max) ? cap_c : cap_c - kLevelThreads - 64;
+
+        BitMap bm;
+        HashMap hm;
+        if (kMap == kMapBitmap) {
+            bm.bits = (uint32_t*)mapr;
+            bm.words = A.bm_words;
+            bm.d = d;
+        } else {
+            hm.cap = label_cap_for(A.lab_size[u]);
+            hm.keys = (uint32_t*)mapr;
+            hm.lvl = (uint16_t*)(mapr + (size_t)hm.cap * 4);
+        }
+
+        for (uint32_t i = tid; i < cap_c; i += kLevelThreads) {
+            ckeys[i] = kEmpty;
+            ccnt[i] = 0ull;
+        }
+        if (kMap == kMapBitmap) bm.clear(); else hm.clear();
+        if (tid == 0) {
+            s_nkeys = 0;
+            s_abort = 0;
+            s_m = 0;
+            s_next = 0;
+            s_nsurv = 0;
+        }
+        __syncthreads();
+
+        // 1. label map of L_<d(u)
+        for (int l = 0; l < d; ++l) {
+            const uint64_t s = __ldg(A.seg + (int64_t)l * n + u);
+            const uint32_t len = seg_len(s);
+            const uint32_t* hs = A.hub_arena + seg_start(s);
+            for (uint32_t i = tid; i < len; i += kLevelThreads) {
+                const uint32_t x = __ldg(hs + i) & kHubMask;
+                if (kMap == kMapBitmap) bm.insert(x, l); else hm.insert(x, l);
+            }
+        }
+        __syncthreads();
+
+        // 2. pull with the membership filter, merged per hub
+        const int64_t a0 = A.rp[u], a1 = A.rp[u + 1];
+        for (int64_t ca = a0; ca < a1; ca += kArcChunk) {
+            const int nc = (int)((a1 - ca) < kArcChunk ? (a1 - ca) : kArcChunk);
+            if (tid < nc) {
+                const uint32_t c = __ldg(A.cnt_arc + ca + tid);
+                pfx[tid] = c;
+                st[tid] = c ? seg_start(__ldg(seg_prev + __ldg(A.col + ca + tid))) : 0ull;
+            }
+            __syncthreads();
+            const long long total = block_excl_scan(pfx, nc, s_wsum);
+            for (long long cb = (long long)warp * 32 * kGatherUnroll; cb < total;
+                 cb += (long long)kWarps * 32 * kGatherUnroll) {
+                if (__shfl_sync(0xFFFFFFFFu, *(volatile int*)&s_abort, 0)) break;
+                int lo = 0, hi = nc;  // last arc whose first entry is <= cb
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pfx[mid] <= cb) lo = mid; else hi = mid;
+                }
+                int j = lo;
+                uint32_t hw[kGatherUnroll];
+                uint64_t pos[kGatherUnroll];
+                bool ok[kGatherUnroll];
+#pragma unroll
+                for (int t = 0; t < kGatherUnroll; ++t) {
+                    const long long i = cb + t * 32 + lane;
+                    ok[t] = i < total;
+                    if (ok[t]) {
+                        while (pfx[j + 1] <= i) ++j;
+                        pos[t] = st[j] + (uint64_t)(i - pfx[j]);
+                        hw[t] = __ldg(A.hub_arena + pos[t]);
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < kGatherUnroll; ++t)
+                    if (ok[t]) {
+                        const uint32_t h = hw[t] & kHubMask;
+                        ok[t] = !(kMap == kMapBitmap ? bm.member(h) : hm.member(h));
+                    }
+                uint64_t cv[kGatherUnroll];
+#pragma unroll
+                for (int t = 0; t < kGatherUnroll; ++t)
+                    if (ok[t]) cv[t] = __ldg((const unsigned long long*)A.cnt_arena + pos[t]);
+#pragma unroll
+                for (int t = 0; t < kGatherUnroll; ++t)
+                    if (ok[t]) cand_insert(ckeys, ccnt, cap_c, limit, hw[t] & kHubMask, cv[t], hw[t] >> 31, &s_nkeys,
+                                           &s_abort);
+            }
+            __syncthreads();
+            if (s_abort) break;
+        }
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) {
+                const int p = atomicAdd(&A.stt->n_retry, 1);
+                A.retry_list[p] = (int32_t)u;
+                atomicMax(&A.stt->need_cap_c, (unsigned long long)cand_cap_for(raw, u, 1u << 30));
+                atomicMax(&A.stt->need_cap_u, (unsigned long long)label_cap_for(A.lab_size[u]));
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // candidate list
+        for (uint32_t slot = tid; slot < cap_c; slot += kLevelThreads)
+            if (ckeys[slot] != kEmpty) list[atomicAdd(&s_m, 1)] = slot;
+        __syncthreads();
+        const int M = s_m;
+
+        // 3. prune rule 2 over levels 1..d-2 of each candidate's label
+        if (d >= 3) {
+            for (;;) {
+                int c = 0;
+                if (glane == 0) c = atomicAdd(&s_next, 1);
+                c = tile.shfl(c, 0);
+                if (c >= M) break;
+                const uint32_t slot = list[c];
+                const uint32_t h = ckeys[slot] & kHubMask;
+                bool pruned = false;
+                for (int k = 1; k <= d - 2 && !pruned; ++k) {
+                    const uint64_t s = __ldg(A.seg + (int64_t)k * n + h);
+                    const uint32_t len = seg_len(s);
+                    const uint32_t* xs = A.hub_arena + seg_start(s);
+                    const int thr = d - 1 - k;
+                    for (uint32_t b = 0; b < len && !pruned; b += kProbeGroup * kProbeUnroll) {
+                        uint32_t x[kProbeUnroll];
+#pragma unroll
+                        for (int t = 0; t < kProbeUnroll; ++t) {
+                            const uint32_t i = b + t * kProbeGroup + glane;
+                            x[t] = i < len ? (__ldg(xs + i) & kHubMask) : kEmpty;
+                        }
+                        bool hit = false;
+#pragma unroll
+                        for (int t = 0; t < kProbeUnroll; ++t)
+                            if (x[t] != kEmpty)
+                                hit |= kMap == kMapBitmap ? bm.within(x[t], thr) : hm.within(x[t], thr);
+                        pruned = tile.any(hit);
+                    }
+                }
+                if (pruned && glane == 0) list[c] = slot | kPrunedBit;
+            }
+            __syncthreads();
+        }
+
+        // 4. survivors: hub-sorted, appended as L_d(u)
+        for (int c = tid; c < M; c += kLevelThreads) {
+            const uint32_t slot = list[c];
+            if (!(slot & kPrunedBit))
+                sortbuf[atomicAdd(&s_nsurv, 1)] = ((unsigned long long)(ckeys[slot] & kHubMask) << 32) | slot;
+        }
+        __syncthreads();
+        const int S = s_nsurv;
+        if (S > 0) {
+            const uint32_t P = pow2_ceil((uint64_t)S);
+            for (uint32_t i = S + tid; i < P; i += kLevelThreads) sortbuf[i] = ~0ull;
+            __syncthreads();
+            block_bitonic_sort(sortbuf, P);
+            if (tid == 0) {
+                const unsigned long long b0 = atomicAdd(&A.stt->bump, (unsigned long long)S);
+                if (b0 + S > A.arena_cap) atomicOr(&A.stt->arena_overflow, 1);
+                s_base = b0;
+            }
+            __syncthreads();
+            const unsigned long long b0 = s_base;
+            if (b0 + S <= A.arena_cap) {
+                for (int i = tid; i < S; i += kLevelThreads) {
+                    const uint32_t slot = (uint32_t)sortbuf[i];
+                    const uint32_t key = ckeys[slot];
+                    A.hub_arena[b0 + i] = (key & kHubMask) | (key & kOvfBit);
+                    A.cnt_arena[b0 + i] = ccnt[slot];
+                }
+                if (tid == 0) A.seg_out[u] = seg_pack(b0, (uint32_t)S);
+            }
+        }
+        if (tid == 0) atomicAdd(&A.stt->unique_total, (unsigned long long)s_nkeys);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+
+cudaError_t launch_arc_src(const int64_t* rp, int64_t n, int32_t* arc_src, cudaStream_t st) {
+    k_arc_src<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(rp, n, arc_src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost(int d, int64_t n, int64_t arcs, const int64_t* rp, const int32_t* col,
+                        const int32_t* arc_src, const uint64_t* seg_prev, const uint32_t* hub_arena,
+                        uint32_t* cnt_arc, int64_t* raw_u, int64_t* lab_size, LevelStatus* stt,
+                        int64_t label_limit, int32_t* glist, int32_t* items, cudaStream_t st, int64_t* launches) {
+    cudaError_t e = cudaMemsetAsync(raw_u, 0, n * 8, st);
+    if (e != cudaSuccess) return e;
+    if (arcs > 0)
+        k_cost_arcs<<<(unsigned)((arcs + 255) / 256), 256, 0, st>>>(arcs, arc_src, col, seg_prev, hub_arena, cnt_arc,
+                                                                     (unsigned long long*)raw_u);
+    k_cost_vertices<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, rp, seg_prev, raw_u, lab_size, stt, label_limit,
+                                                                  glist);
+    k_bucket_base<<<1, 32, 0, st>>>(stt);
+    k_bucket_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, raw_u, lab_size, stt, label_limit, items);
+    if (launches) *launches += (arcs > 0) + 3;
+    return cudaGetLastError();
+}
+
+cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy) {
+    const void* f = map_kind == kMapBitmap ? (const void*)k_level<kMapBitmap, false>
+                                           : (const void*)k_level<kMapHash, false>;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, f, kLevelThreads, smem_bytes);
+}
+
+cudaError_t launch_level(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,
+                         cudaStream_t st) {
+    if (offchip)
+        k_level<kMapHash, true><<<grid, kLevelThreads, 0, st>>>(A);
+    else if (map_kind == kMapBitmap)
+        k_level<kMapBitmap, false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
+    else
+        k_level<kMapHash, false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace pspc

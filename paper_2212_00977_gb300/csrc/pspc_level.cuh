@@ -1,0 +1,115 @@
+// Internal interface between the build orchestration (pspc_build.cu) and
+// the per-level kernels (pspc_level.cu): status record, kernel arguments,
+// the on-chip table layout and the host-side launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pspc_internal.cuh"
+
+namespace pspc {
+
+constexpr int kLevelThreads = 512;
+constexpr int kArcChunk = kLevelThreads;  // arcs staged per gather chunk
+constexpr int kBuckets = 64;
+constexpr size_t kBitmapBudget = 40 * 1024;  // on-chip bytes for the level bitmaps
+
+struct LevelStatus {
+    unsigned long long raw_total;
+    unsigned long long unique_total;
+    unsigned long long bump;        // arena fill after this level
+    unsigned long long need_cap_c;  // largest candidate table of the off-chip class
+    unsigned long long need_cap_u;  // largest label table of the off-chip class
+    unsigned long long active_arcs;
+    int n_active;
+    int n_smem;
+    int n_global;
+    int n_retry;
+    int arena_overflow;
+    int work_smem;
+    int work_global;
+    int pad;
+    int bucket_cnt[kBuckets];
+    int bucket_base[kBuckets];
+    int bucket_fill[kBuckets];
+};
+
+struct LevelArgs {
+    int d;
+    int64_t n;
+    const int64_t* rp;
+    const int32_t* col;
+    const uint32_t* cnt_arc;
+    const uint64_t* seg;  // [levels][n]
+    uint64_t* seg_out;    // row d
+    uint32_t* hub_arena;
+    uint64_t* cnt_arena;
+    unsigned long long arena_cap;
+    const int64_t* raw_u;
+    const int64_t* lab_size;
+    const int32_t* items;
+    int n_items;
+    int* work;
+    LevelStatus* stt;
+    int32_t* retry_list;  // appended at retry_list[k]
+    uint32_t cap_c_max;   // candidate table slots (on chip, or per-CTA scratch)
+    uint32_t cap_u_max;   // label hash slots (hash map kind)
+    uint32_t bm_words;    // words per level bitmap (bitmap map kind)
+    uint8_t* gscratch;    // per-CTA table memory when the tables are off chip
+    size_t gscratch_stride;
+};
+
+// Table layout (on chip, or in per-CTA device scratch). The map region also
+// holds the survivor sort buffer once the prune step is done.
+struct LevelLayout {
+    size_t cnt, key, map, list, st, pfx, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline LevelLayout level_layout(uint32_t cap_c, size_t map_bytes) {
+    LevelLayout L;
+    size_t p = 0;
+    L.cnt = p;
+    p += (size_t)cap_c * 8;
+    L.key = p;
+    p = align16(p + (size_t)cap_c * 4);
+    L.map = p;
+    p = align16(p + (map_bytes > (size_t)cap_c * 8 ? map_bytes : (size_t)cap_c * 8));
+    L.list = p;
+    p = align16(p + (size_t)cap_c * 4);
+    L.st = p;
+    p = align16(p + (size_t)kArcChunk * 8);
+    L.pfx = p;
+    p = align16(p + (size_t)(kArcChunk + 1) * 8);
+    L.total = p;
+    return L;
+}
+
+__host__ __device__ inline size_t bitmap_bytes(int d, uint32_t bm_words) { return (size_t)(d - 1) * bm_words * 4; }
+__host__ __device__ inline size_t hashmap_bytes(uint32_t cap_u) { return (size_t)cap_u * 6; }
+
+__host__ __device__ inline uint32_t cand_cap_for(int64_t raw, int64_t u, uint32_t cap_max) {
+    const int64_t bound = raw < u ? raw : u;  // distinct hubs <= pulled entries, and < u
+    const uint64_t want = (uint64_t)(2 * bound) < 64ull ? 64ull : (uint64_t)(2 * bound);
+    return want >= cap_max ? cap_max : pow2_ceil(want);
+}
+__host__ __device__ inline uint32_t label_cap_for(int64_t lab) {
+    const uint64_t want = (uint64_t)(lab + lab / 3 + 1);
+    return pow2_ceil(want < 64ull ? 64ull : want);
+}
+
+enum MapKind { kMapBitmap = 0, kMapHash = 1 };
+
+// Launchers (pspc_level.cu). Each returns a CUDA error code of the launch.
+cudaError_t launch_arc_src(const int64_t* rp, int64_t n, int32_t* arc_src, cudaStream_t st);
+cudaError_t launch_cost(int d, int64_t n, int64_t arcs, const int64_t* rp, const int32_t* col,
+                        const int32_t* arc_src, const uint64_t* seg_prev, const uint32_t* hub_arena,
+                        uint32_t* cnt_arc, int64_t* raw_u, int64_t* lab_size, LevelStatus* stt,
+                        int64_t label_limit, int32_t* glist, int32_t* items, cudaStream_t st, int64_t* launches);
+cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy);
+cudaError_t launch_level(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,
+                         cudaStream_t st);
+
+}  // namespace pspc
