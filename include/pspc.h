@@ -163,6 +163,13 @@ int pspc_stats(const pspc_index* ix, pspc_stats_t* s);
 int pspc_level_stats(const pspc_index* ix, pspc_level_stat_t* out, int32_t cap,
                      int32_t* levels);
 
+/*
+ * pspc_set_query_group -- tuning hook for pspc_query: the number of lanes
+ * that merge-join one pair (8, 16 or 32; 0 = chosen from the average label
+ * size). Results do not depend on it. Errors: PSPC_E_INVAL.
+ */
+int pspc_set_query_group(pspc_index* ix, int32_t lanes);
+
 /* pspc_free -- release an index and all its device memory; NULL is a no-op. */
 void pspc_free(pspc_index* ix);
 

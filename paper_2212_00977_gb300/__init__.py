@@ -71,6 +71,7 @@ _SIGS = {
     "pspc_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "pspc_level_stats": (ctypes.c_int, [_P, ctypes.POINTER(LevelStat), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
+    "pspc_set_query_group": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pspc_free": (None, [_P]),
     "pspc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -190,6 +191,12 @@ class Index:
         if rc != PSPC_OK:
             raise PSPCError(rc, "pspc_query")
         return dist, count, overflow
+
+    def set_query_group(self, lanes: int) -> None:
+        """Lanes per pair in pspc_query (8, 16, 32; 0 = automatic)."""
+        rc = load().pspc_set_query_group(self._h, int(lanes))
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_set_query_group")
 
     def stats(self) -> dict:
         s = Stats()

@@ -11,6 +11,7 @@
 // hub, bit 31 overflow flag) and a uint64 count; the distance is the level.
 // The per-level kernels live in pspc_level.cu.
 #include <cuda_runtime.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -46,27 +47,24 @@ __global__ void k_check_rowptr(const int64_t* __restrict__ rp, int64_t n, int* e
     if (v < n && rp[v] > rp[v + 1]) atomicOr(err, 1);
 }
 
-// Warp per vertex: ids in range, no self-loop, rows strictly ascending, and
-// every arc has its reverse (binary search in the neighbour's row).
-__global__ void k_check_arcs(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t n,
-                             int* err) {
-    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (u >= n) return;
-    const int64_t a0 = rp[u], a1 = rp[u + 1];
-    for (int64_t a = a0 + lane; a < a1; a += 32) {
-        const int32_t v = col[a];
-        if (v < 0 || v >= n || v == u || (a + 1 < a1 && col[a + 1] <= v)) {
-            atomicOr(err, 1);
-            continue;
-        }
-        int64_t lo = rp[v], hi = rp[v + 1];
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (col[mid] < u) lo = mid + 1; else hi = mid;
-        }
-        if (lo == rp[v + 1] || col[lo] != (int32_t)u) atomicOr(err, 1);
+// Thread per arc u->v: ids in range, no self-loop, rows strictly ascending,
+// and the reverse arc v->u exists (binary search in the row of v).
+__global__ void k_check_arcs(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ arc_src, int64_t arcs, int64_t n, int* err) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= arcs) return;
+    const int32_t u = arc_src[a];
+    const int32_t v = col[a];
+    if (v < 0 || v >= n || v == u || (a + 1 < rp[u + 1] && col[a + 1] <= v)) {
+        atomicOr(err, 1);
+        return;
     }
+    int64_t lo = rp[v], hi = rp[v + 1];
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < u) lo = mid + 1; else hi = mid;
+    }
+    if (lo == rp[v + 1] || col[lo] != u) atomicOr(err, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -90,6 +88,139 @@ __global__ void k_relabel_arcs(const int64_t* __restrict__ rp, const int32_t* __
     const int64_t a0 = rp[v], deg = rp[v + 1] - a0;
     const int64_t b0 = rp_r[rank[v]];
     for (int64_t i = lane; i < deg; i += 32) col_r[b0 + i] = rank[col[a0 + i]];
+}
+
+// Rank-space rows sorted ascending (highest-ranked neighbours first). Rows
+// of up to 32 arcs are sorted by one warp in registers, up to kRowSmem on
+// chip by the block; longer rows are listed for k_sort_big_rows.
+constexpr int kRowThreads = 128;
+constexpr int kRowSmem = 4096;
+
+__global__ void __launch_bounds__(kRowThreads) k_sort_rows(const int64_t* __restrict__ rp, int32_t* __restrict__ col,
+                                                           int64_t n, int32_t* __restrict__ big, int* n_big) {
+    __shared__ int32_t s[kRowSmem];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t a0 = rp[r];
+        const int64_t deg = rp[r + 1] - a0;
+        if (deg <= 1) continue;
+        if (deg <= 32) {
+            if (tid < 32) {
+                int32_t v = lane < deg ? col[a0 + lane] : INT32_MAX;
+                for (int k = 2; k <= 32; k <<= 1)
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        const int32_t w = __shfl_xor_sync(0xFFFFFFFFu, v, j);
+                        const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
+                        v = keep_min ? min(v, w) : max(v, w);
+                    }
+                if (lane < deg) col[a0 + lane] = v;
+            }
+        } else if (deg <= kRowSmem) {
+            const uint32_t P = pow2_ceil((uint64_t)deg);
+            for (uint32_t i = tid; i < P; i += kRowThreads) s[i] = i < deg ? col[a0 + i] : INT32_MAX;
+            __syncthreads();
+            for (uint32_t k = 2; k <= P; k <<= 1)
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t i = tid; i < P; i += kRowThreads) {
+                        const uint32_t ixj = i ^ j;
+                        if (ixj > i) {
+                            const int32_t x = s[i], y = s[ixj];
+                            if ((x > y) == ((i & k) == 0)) {
+                                s[i] = y;
+                                s[ixj] = x;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            for (uint32_t i = tid; i < deg; i += kRowThreads) col[a0 + i] = s[i];
+            __syncthreads();
+        } else if (tid == 0) {
+            big[atomicAdd(n_big, 1)] = (int32_t)r;
+        }
+    }
+}
+
+// Long rows: ids in a row are distinct, so a bitmap over [0, n) in device
+// scratch, read back in order with a popcount prefix, sorts the row.
+__global__ void __launch_bounds__(kRowThreads) k_sort_big_rows(const int64_t* __restrict__ rp, int32_t* __restrict__ col,
+                                                               int64_t n, const int32_t* __restrict__ big, int n_big,
+                                                               uint32_t* __restrict__ scratch) {
+    __shared__ long long s_run[kRowThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t W = (uint32_t)((n + 31) >> 5);
+    uint32_t* bm = scratch + (size_t)blockIdx.x * W;
+    for (int b = blockIdx.x; b < n_big; b += gridDim.x) {
+        const int64_t r = big[b];
+        const int64_t a0 = rp[r], deg = rp[r + 1] - a0;
+        for (uint32_t i = tid; i < W; i += kRowThreads) bm[i] = 0u;
+        __syncthreads();
+        for (int64_t i = tid; i < deg; i += kRowThreads) {
+            const int32_t v = col[a0 + i];
+            atomicOr(&bm[v >> 5], 1u << (v & 31));
+        }
+        __syncthreads();
+        const uint32_t per = (W + kRowThreads - 1) / kRowThreads;
+        const uint32_t w0 = tid * per, w1 = w0 + per < W ? w0 + per : W;
+        long long cnt = 0;
+        for (uint32_t i = w0; i < w1; ++i) cnt += __popc(bm[i]);
+        long long incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_run[warp] = incl;
+        __syncthreads();
+        long long run = incl - cnt;
+        for (int w = 0; w < warp; ++w) run += s_run[w];
+        for (uint32_t i = w0; i < w1; ++i) {
+            uint32_t bits = bm[i];
+            while (bits) {
+                const int bit = __ffs(bits) - 1;
+                bits &= bits - 1;
+                col[a0 + run++] = (int32_t)(i * 32 + bit);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Level 1 without a pull: L_1(u) is the set of neighbours ranked above u,
+// each with one path -- the prefix of u's sorted row below u.
+__global__ void k_level1_counts(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t n,
+                                int64_t* __restrict__ len1, unsigned long long* active) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int64_t lo = rp[u], hi = rp[u + 1];
+    const int64_t a0 = lo;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < u) lo = mid + 1; else hi = mid;
+    }
+    len1[u] = lo - a0;
+    if (lo > a0) {
+        atomicAdd(&active[0], 1ull);
+        atomicAdd(&active[1], (unsigned long long)(rp[u + 1] - a0));
+    }
+}
+
+__global__ void k_level1_write(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t n,
+                               const int64_t* __restrict__ pos1, unsigned long long base,
+                               uint32_t* __restrict__ hub_arena, uint64_t* __restrict__ cnt_arena,
+                               uint64_t* __restrict__ seg1, int64_t* __restrict__ lab_size) {
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= n) return;
+    const int64_t p0 = pos1[u], len = pos1[u + 1] - p0;
+    const int64_t a0 = rp[u];
+    for (int64_t i = lane; i < len; i += 32) {
+        hub_arena[base + p0 + i] = (uint32_t)col[a0 + i];
+        cnt_arena[base + p0 + i] = 1ull;
+    }
+    if (lane == 0) {
+        seg1[u] = len ? seg_pack(base + p0, (uint32_t)len) : 0ull;
+        lab_size[u] = 1;  // L_<2(u) before level 1 is added: the level-0 entry
+    }
 }
 
 // Level 0: L_0(v) = {(v, 0, 1)}.
@@ -212,16 +343,80 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinArgs F) {
     if (tid == 0 && s_ovf) atomicAdd(F.n_ovf, s_ovf);
 }
 
+// Few levels: every level segment of a vertex is already hub-sorted, so the
+// final slot of an entry is its index in its own segment plus, for every
+// other level, the number of hubs there that rank above it (binary search
+// over an on-chip copy of the vertex's hubs). Hubs are unique per vertex.
+constexpr int kFinMergeLevels = 16;
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize_merge(const FinArgs F) {
+    extern __shared__ __align__(16) uint32_t s_hub[];  // kFinSmemKeys hub words
+    __shared__ unsigned long long s_st[kFinMergeLevels];
+    __shared__ int s_off[kFinMergeLevels + 1];
+    __shared__ unsigned long long s_ovf;
+    const int tid = threadIdx.x;
+    const int L = F.levels;
+    if (tid == 0) s_ovf = 0;
+    unsigned long long novf = 0;
+    for (int64_t u = blockIdx.x; u < F.n; u += gridDim.x) {
+        const int64_t o0 = F.off[u];
+        const int T = (int)(F.off[u + 1] - o0);
+        if (T > kFinSmemKeys) continue;  // uniform: sorted by the off-chip pass
+        if (tid < L) {
+            const uint64_t s = __ldg(F.seg + (int64_t)tid * F.n + u);
+            s_st[tid] = seg_start(s);
+            s_off[tid + 1] = (int)seg_len(s);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            s_off[0] = 0;
+            for (int l = 0; l < L; ++l) s_off[l + 1] += s_off[l];
+        }
+        __syncthreads();
+        for (int i = tid; i < T; i += kFinThreads) {
+            int l = 0;
+            while (s_off[l + 1] <= i) ++l;
+            s_hub[i] = __ldg(F.hub_arena + s_st[l] + (i - s_off[l]));
+        }
+        __syncthreads();
+        for (int i = tid; i < T; i += kFinThreads) {
+            int l = 0;
+            while (s_off[l + 1] <= i) ++l;
+            const uint32_t w = s_hub[i];
+            const uint32_t h = w & kHubMask;
+            int pos = i - s_off[l];
+            for (int l2 = 0; l2 < L; ++l2) {
+                if (l2 == l) continue;
+                int lo = s_off[l2], hi = s_off[l2 + 1];
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((s_hub[mid] & kHubMask) < h) lo = mid + 1; else hi = mid;
+                }
+                pos += lo - s_off[l2];
+            }
+            const uint32_t ovf = w >> 31;
+            novf += ovf;
+            F.hub[o0 + pos] = (int32_t)h;
+            F.dist[o0 + pos] = (uint16_t)(l | (ovf << 15));
+            F.cnt[o0 + pos] = __ldg((const unsigned long long*)F.cnt_arena + s_st[l] + (i - s_off[l]));
+        }
+        __syncthreads();
+    }
+    if (novf) atomicAdd(&s_ovf, novf);
+    __syncthreads();
+    if (tid == 0 && s_ovf) atomicAdd(F.n_ovf, s_ovf);
+}
+
 // ---------------------------------------------------------------------------
 // Host orchestration.
 
 template <typename T>
 static cudaError_t dalloc(T** p, size_t count, cudaStream_t st) {
-    return cudaMallocAsync((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
+    return dev_alloc((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
 }
 template <typename T>
 static void dfree(T*& p, cudaStream_t st) {
-    if (p) cudaFreeAsync(p, st);
+    dev_free(p, st);
     p = nullptr;
 }
 
@@ -262,7 +457,8 @@ struct Builder {
     int32_t* items = nullptr;
     int32_t* glist = nullptr;
     LevelStatus* stt = nullptr;
-    LevelStatus* hstt = nullptr;  // pinned
+    LevelStatus hs;               // host copy of the level status
+    LevelStatus* hstt = &hs;
     int* err = nullptr;
     uint8_t* gscratch = nullptr;
     size_t gscratch_bytes = 0;
@@ -291,15 +487,14 @@ struct Builder {
         dfree(stt, st);
         dfree(err, st);
         dfree(gscratch, st);
-        if (hstt) cudaFreeHost(hstt);
         if (ek0) cudaEventDestroy(ek0);
         if (ek1) cudaEventDestroy(ek1);
-        cudaFree(out.rank);
-        cudaFree(out.order);
-        cudaFree(out.off);
-        cudaFree(out.hub);
-        cudaFree(out.dist);
-        cudaFree(out.cnt);
+        dfree(out.rank, st);
+        dfree(out.order, st);
+        dfree(out.off, st);
+        dfree(out.hub, st);
+        dfree(out.dist, st);
+        dfree(out.cnt, st);
         cudaStreamSynchronize(st);
     }
 
@@ -356,8 +551,12 @@ struct Builder {
         PSPC_TRY_CUDA(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st));
         PSPC_TRY_CUDA(cudaStreamSynchronize(st));
         if (h) return PSPC_E_INVAL;
-        k_check_arcs<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(rp, col, n, err);
-        out.launches += 1;
+        PSPC_TRY_CUDA(dalloc(&arc_src, arcs, st));
+        if (arcs > 0) {
+            PSPC_TRY_CUDA(launch_arc_src(rp, n, arc_src, st));
+            k_check_arcs<<<(unsigned)((arcs + 255) / 256), 256, 0, st>>>(rp, col, arc_src, arcs, n, err);
+            out.launches += 2;
+        }
         PSPC_TRY_CUDA(cudaGetLastError());
         PSPC_TRY_CUDA(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st));
         PSPC_TRY_CUDA(cudaStreamSynchronize(st));
@@ -374,7 +573,74 @@ struct Builder {
         int rc = exclusive_scan_i64(rp_r, n, st, &out.launches);
         if (rc) return rc;
         k_relabel_arcs<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(rp, col, rank, n, rp_r, col_r);
-        return cuda_status(cudaGetLastError());
+        PSPC_TRY_CUDA(cudaGetLastError());
+        return sort_rows();
+    }
+
+    // Sorts every rank-space row ascending (highest-ranked neighbour first).
+    int sort_rows() {
+        int32_t* big = nullptr;
+        int* nbig = nullptr;
+        PSPC_TRY_CUDA(dalloc(&big, n, st));
+        PSPC_TRY_CUDA(dalloc(&nbig, 1, st));
+        PSPC_TRY_CUDA(cudaMemsetAsync(nbig, 0, sizeof(int), st));
+        const int grid = (int)std::min<int64_t>(n, (int64_t)sms * 16);
+        k_sort_rows<<<grid, kRowThreads, 0, st>>>(rp_r, col_r, n, big, nbig);
+        out.launches += 1;
+        PSPC_TRY_CUDA(cudaGetLastError());
+        int hbig = 0;
+        PSPC_TRY_CUDA(cudaMemcpyAsync(&hbig, nbig, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PSPC_TRY_CUDA(cudaStreamSynchronize(st));
+        int rc = PSPC_OK;
+        if (hbig > 0) {
+            const int g2 = std::min(hbig, sms);
+            const size_t W = (size_t)((n + 31) / 32);
+            uint32_t* scratch = nullptr;
+            PSPC_TRY_CUDA(dalloc(&scratch, W * g2, st));
+            k_sort_big_rows<<<g2, kRowThreads, 0, st>>>(rp_r, col_r, n, big, hbig, scratch);
+            out.launches += 1;
+            rc = cuda_status(cudaGetLastError());
+            dfree(scratch, st);
+        }
+        dfree(big, st);
+        dfree(nbig, st);
+        return rc;
+    }
+
+    // Level 1 (distance 1): the prefix of each sorted row below the vertex.
+    int level1(unsigned long long& bump, pspc_level_stat_t& ls) {
+        int64_t* len1 = nullptr;
+        unsigned long long* act = nullptr;
+        PSPC_TRY_CUDA(dalloc(&len1, n + 1, st));
+        PSPC_TRY_CUDA(dalloc(&act, 2, st));
+        PSPC_TRY_CUDA(cudaMemsetAsync(act, 0, 16, st));
+        k_level1_counts<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rp_r, col_r, n, len1, act);
+        out.launches += 1;
+        PSPC_TRY_CUDA(cudaGetLastError());
+        int rc = exclusive_scan_i64(len1, n, st, &out.launches);
+        if (rc) return rc;
+        int64_t total = 0;
+        unsigned long long hact[2] = {0, 0};
+        PSPC_TRY_CUDA(cudaMemcpyAsync(&total, len1 + n, 8, cudaMemcpyDeviceToHost, st));
+        PSPC_TRY_CUDA(cudaMemcpyAsync(hact, act, 16, cudaMemcpyDeviceToHost, st));
+        PSPC_TRY_CUDA(cudaStreamSynchronize(st));
+        if (bump + (unsigned long long)total > arena_cap) {
+            if ((rc = grow_arena(bump + total, bump))) return rc;
+        }
+        k_level1_write<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(rp_r, col_r, n, len1, bump, hub_arena,
+                                                                          cnt_arena, seg + n, lab_size);
+        out.launches += 1;
+        PSPC_TRY_CUDA(cudaGetLastError());
+        dfree(len1, st);
+        dfree(act, st);
+        bump += (unsigned long long)total;
+        ls.raw_candidates = total;
+        ls.unique_candidates = total;
+        ls.entries = total;
+        ls.active_vertices = (int64_t)hact[0];
+        ls.active_arcs = (int64_t)hact[1];
+        ls.kernel_ms = 0.f;
+        return PSPC_OK;
     }
 
     int grow_arena(unsigned long long need, unsigned long long keep) {
@@ -534,13 +800,11 @@ struct Builder {
         rc = grow_arena(std::max<unsigned long long>(cap0, (unsigned long long)n + 1024), 0);
         if (rc) return rc;
         PSPC_TRY_CUDA(dalloc(&cnt_arc, arcs, st));
-        PSPC_TRY_CUDA(dalloc(&arc_src, arcs, st));
         PSPC_TRY_CUDA(dalloc(&raw_u, n, st));
         PSPC_TRY_CUDA(dalloc(&lab_size, n, st));
         PSPC_TRY_CUDA(dalloc(&items, n, st));
         PSPC_TRY_CUDA(dalloc(&glist, 2 * n, st));
         PSPC_TRY_CUDA(dalloc(&stt, 1, st));
-        PSPC_TRY_CUDA(cudaMallocHost((void**)&hstt, sizeof(LevelStatus)));
         PSPC_TRY_CUDA(cudaMemsetAsync(lab_size, 0, n * 8, st));
         PSPC_TRY_CUDA(launch_arc_src(rp_r, n, arc_src, st));
         out.launches += 1;
@@ -564,6 +828,22 @@ struct Builder {
             if ((rc = ensure_seg_levels(d + 1))) break;
             if ((rc = plan_level(d, plan))) break;
             cudaEventRecord(e0, st);
+            if (d == 1) {
+                pspc_level_stat_t ls;
+                cudaMemsetAsync(seg + n, 0, n * 8, st);
+                if ((rc = level1(bump, ls))) break;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ls.ms, e0, e1);
+                out.lstats.push_back(ls);
+                if (o.verbose)
+                    fprintf(stderr, "pspc level 1: entries %lld active %lld %.3f ms\n", (long long)ls.entries,
+                            (long long)ls.active_vertices, ls.ms);
+                if (ls.entries == 0) break;
+                lvl_base.push_back(bump);
+                levels = 2;
+                continue;
+            }
             cudaMemsetAsync(seg + (int64_t)d * n, 0, n * 8, st);
             cudaMemsetAsync(stt, 0, sizeof(LevelStatus), st);
             cudaMemcpyAsync(&stt->bump, &lvl_base[d], 8, cudaMemcpyHostToDevice, st);
@@ -629,7 +909,7 @@ struct Builder {
 
     int finalize() {
         const int L = out.levels;
-        PSPC_TRY_CUDA(cudaMalloc(&out.off, (n + 1) * 8));
+        PSPC_TRY_CUDA(dalloc(&out.off, n + 1, st));
         int32_t* big = nullptr;
         int* ctr = nullptr;  // [0] = n_big, [1] = work
         unsigned long long* d_lvl = nullptr;
@@ -651,9 +931,9 @@ struct Builder {
         PSPC_TRY_CUDA(cudaMemcpyAsync(hbig, ctr, 8, cudaMemcpyDeviceToHost, st));
         PSPC_TRY_CUDA(cudaStreamSynchronize(st));
         const int64_t E = out.entries;
-        PSPC_TRY_CUDA(cudaMalloc(&out.hub, std::max<int64_t>(E, 1) * 4));
-        PSPC_TRY_CUDA(cudaMalloc(&out.dist, std::max<int64_t>(E, 1) * 2));
-        PSPC_TRY_CUDA(cudaMalloc(&out.cnt, std::max<int64_t>(E, 1) * 8));
+        PSPC_TRY_CUDA(dalloc(&out.hub, E, st));
+        PSPC_TRY_CUDA(dalloc(&out.dist, E, st));
+        PSPC_TRY_CUDA(dalloc(&out.cnt, E, st));
         FinArgs F;
         memset(&F, 0, sizeof(F));
         F.n = n;
@@ -667,10 +947,19 @@ struct Builder {
         F.dist = out.dist;
         F.cnt = out.cnt;
         F.n_ovf = n_ovf;
-        const size_t fin_smem = (size_t)kFinSmemKeys * 8;
-        PSPC_TRY_CUDA(cudaFuncSetAttribute(k_finalize<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fin_smem));
-        const int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
-        k_finalize<false><<<grid, kFinThreads, fin_smem, st>>>(F);
+        if (L <= kFinMergeLevels) {
+            const size_t fin_smem = (size_t)kFinSmemKeys * 4;
+            PSPC_TRY_CUDA(cudaFuncSetAttribute(k_finalize_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)fin_smem));
+            const int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
+            k_finalize_merge<<<grid, kFinThreads, fin_smem, st>>>(F);
+        } else {
+            const size_t fin_smem = (size_t)kFinSmemKeys * 8;
+            PSPC_TRY_CUDA(cudaFuncSetAttribute(k_finalize<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)fin_smem));
+            const int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
+            k_finalize<false><<<grid, kFinThreads, fin_smem, st>>>(F);
+        }
         out.launches += 1;
         PSPC_TRY_CUDA(cudaGetLastError());
         if (hbig[0] > 0) {
@@ -703,8 +992,8 @@ struct Builder {
         dfree(d_lvl, st);
         dfree(n_ovf, st);
         // the index keeps its own copy of the order
-        PSPC_TRY_CUDA(cudaMalloc(&out.rank, n * 4));
-        PSPC_TRY_CUDA(cudaMalloc(&out.order, n * 4));
+        PSPC_TRY_CUDA(dalloc(&out.rank, n, st));
+        PSPC_TRY_CUDA(dalloc(&out.order, n, st));
         PSPC_TRY_CUDA(cudaMemcpyAsync(out.rank, rank, n * 4, cudaMemcpyDeviceToDevice, st));
         PSPC_TRY_CUDA(cudaMemcpyAsync(out.order, order, n * 4, cudaMemcpyDeviceToDevice, st));
         return PSPC_OK;

@@ -52,12 +52,20 @@ struct Index {
     int64_t overflow_entries = 0;
     float build_ms = 0.f;
     int64_t launches = 0;
+    int32_t query_group = 0;  // lanes per query pair; 0 = chosen from label sizes
     std::vector<pspc_level_stat_t> lstats;
 };
 
 // Host-side helpers (pspc_util.cu).
 bool is_device_ptr(const void* p);
 int cuda_status(cudaError_t e);
+
+// Device memory of the library comes from one stream-ordered pool per
+// device, created on first use with an unbounded release threshold so that
+// memory freed by one build or query is reused by the next without going
+// back to the driver. dev_alloc / dev_free are stream-ordered.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
 
 // Exclusive prefix sum of int64 values in place: a[0..n) -> exclusive
 // scan, a[n] = total (a must hold n+1 values). Device memory.

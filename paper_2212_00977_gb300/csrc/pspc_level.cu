@@ -224,6 +224,33 @@ __device__ long long block_excl_scan(long long* a, int n, long long* wsum) {
     return total;
 }
 
+// Exclusive prefix of popcounts of bits[0..W) into wp[0..W); returns the
+// total number of set bits. Each thread owns a contiguous run of words.
+__device__ long long block_excl_scan_popc(const uint32_t* bits, uint32_t* wp, uint32_t W, long long* wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const uint32_t per = (W + blockDim.x - 1) / blockDim.x;
+    const uint32_t w0 = tid * per, w1 = w0 + per < W ? w0 + per : W;
+    long long v = 0;
+    for (uint32_t i = w0; i < w1; ++i) v += __popc(bits[i]);
+    const long long incl = warp_incl_scan64(v);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        long long t = lane < nw ? wsum[lane] : 0;
+        t = warp_incl_scan64(t);
+        if (lane < nw) wsum[lane] = t;
+    }
+    __syncthreads();
+    const long long total = wsum[nw - 1];
+    long long run = incl - v + (warp ? wsum[warp - 1] : 0);
+    for (uint32_t i = w0; i < w1; ++i) {
+        wp[i] = (uint32_t)run;
+        run += __popc(bits[i]);
+    }
+    __syncthreads();
+    return total;
+}
+
 __device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
     for (uint32_t k = 2; k <= P; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -390,8 +417,75 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         __syncthreads();
         const int M = s_m;
 
+        // 3a. d = 3: rule 2 asks for a common neighbour x of u and h ranked
+        // above h (x in L_1(u) and x in L_1(h)). Mark every h in (x, u) adjacent
+        // to some x in L_1(u) -- a range of x's sorted row -- then test each
+        // candidate with one bit instead of scanning L_1(h).
+        bool marked = false;
+        const uint32_t Wm = (uint32_t)((u + 31) >> 5);
+        if (d == 3 && (size_t)Wm * 4 <= (size_t)(L.list - L.map) && M > 0) {
+            uint32_t* mk = (uint32_t*)mapr;
+            for (uint32_t i = tid; i < Wm; i += kLevelThreads) mk[i] = 0u;
+            const uint64_t s1 = __ldg(A.seg + n + u);
+            const uint32_t len1 = seg_len(s1);
+            const uint32_t* xs = A.hub_arena + seg_start(s1);
+            __syncthreads();
+            for (uint32_t c0 = 0; c0 < len1; c0 += kArcChunk) {
+                const int nc = (int)(len1 - c0 < (uint32_t)kArcChunk ? len1 - c0 : (uint32_t)kArcChunk);
+                if (tid < nc) {
+                    const uint32_t x = __ldg(xs + c0 + tid) & kHubMask;
+                    const int64_t r1 = A.rp[x + 1];
+                    int64_t lo = A.rp[x], hi = r1;
+                    while (lo < hi) {  // first neighbour of x ranked below x
+                        const int64_t mid = (lo + hi) >> 1;
+                        if ((uint32_t)__ldg(A.col + mid) <= x) lo = mid + 1; else hi = mid;
+                    }
+                    const int64_t first = lo;
+                    hi = r1;
+                    while (lo < hi) {  // first neighbour of x not ranked above u
+                        const int64_t mid = (lo + hi) >> 1;
+                        if ((int64_t)__ldg(A.col + mid) < u) lo = mid + 1; else hi = mid;
+                    }
+                    pfx[tid] = lo - first;
+                    st[tid] = (uint64_t)first;
+                }
+                __syncthreads();
+                const long long total = block_excl_scan(pfx, nc, s_wsum);
+                for (long long cb = (long long)warp * 32 * kGatherUnroll; cb < total;
+                     cb += (long long)kWarps * 32 * kGatherUnroll) {
+                    int lo = 0, hi = nc;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pfx[mid] <= cb) lo = mid; else hi = mid;
+                    }
+                    int j = lo;
+                    int32_t hv[kGatherUnroll];
+#pragma unroll
+                    for (int t = 0; t < kGatherUnroll; ++t) {
+                        const long long i = cb + t * 32 + lane;
+                        hv[t] = -1;
+                        if (i < total) {
+                            while (pfx[j + 1] <= i) ++j;
+                            hv[t] = __ldg(A.col + st[j] + (uint64_t)(i - pfx[j]));
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < kGatherUnroll; ++t)
+                        if (hv[t] >= 0) atomicOr(&mk[hv[t] >> 5], 1u << (hv[t] & 31));
+                }
+                __syncthreads();
+            }
+            for (int c = tid; c < M; c += kLevelThreads) {
+                const uint32_t slot = list[c];
+                const uint32_t h = ckeys[slot] & kHubMask;
+                if ((mk[h >> 5] >> (h & 31)) & 1u) list[c] = slot | kPrunedBit;
+            }
+            __syncthreads();
+            marked = true;
+        }
+
         // 3. prune rule 2 over levels 1..d-2 of each candidate's label
-        if (d >= 3) {
+        if (d >= 3 && !marked) {
             for (;;) {
                 int c = 0;
                 if (glane == 0) c = atomicAdd(&s_next, 1);
@@ -425,34 +519,76 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             __syncthreads();
         }
 
-        // 4. survivors: hub-sorted, appended as L_d(u)
-        for (int c = tid; c < M; c += kLevelThreads) {
-            const uint32_t slot = list[c];
-            if (!(slot & kPrunedBit))
-                sortbuf[atomicAdd(&s_nsurv, 1)] = ((unsigned long long)(ckeys[slot] & kHubMask) << 32) | slot;
-        }
-        __syncthreads();
-        const int S = s_nsurv;
-        if (S > 0) {
-            const uint32_t P = pow2_ceil((uint64_t)S);
-            for (uint32_t i = S + tid; i < P; i += kLevelThreads) sortbuf[i] = ~0ull;
+        // 4. survivors, hub-sorted, appended as L_d(u). Candidate hubs are < u:
+        // when a bitmap of u bits and its word prefix fit the map region, a
+        // survivor's rank is the prefix of its word plus a popcount; else a
+        // bitonic sort.
+        const uint32_t W = (uint32_t)((u + 31) >> 5);
+        const size_t region = (L.list - L.map);
+        if ((size_t)W * 8 <= region) {
+            uint32_t* sb = (uint32_t*)mapr;
+            uint32_t* wp = sb + W;
+            for (uint32_t i = tid; i < W; i += kLevelThreads) sb[i] = 0u;
             __syncthreads();
-            block_bitonic_sort(sortbuf, P);
-            if (tid == 0) {
-                const unsigned long long b0 = atomicAdd(&A.stt->bump, (unsigned long long)S);
-                if (b0 + S > A.arena_cap) atomicOr(&A.stt->arena_overflow, 1);
-                s_base = b0;
+            for (int c = tid; c < M; c += kLevelThreads) {
+                const uint32_t slot = list[c];
+                if (!(slot & kPrunedBit)) {
+                    const uint32_t h = ckeys[slot] & kHubMask;
+                    atomicOr(&sb[h >> 5], 1u << (h & 31));
+                }
             }
             __syncthreads();
-            const unsigned long long b0 = s_base;
-            if (b0 + S <= A.arena_cap) {
-                for (int i = tid; i < S; i += kLevelThreads) {
-                    const uint32_t slot = (uint32_t)sortbuf[i];
-                    const uint32_t key = ckeys[slot];
-                    A.hub_arena[b0 + i] = (key & kHubMask) | (key & kOvfBit);
-                    A.cnt_arena[b0 + i] = ccnt[slot];
+            const int S = (int)block_excl_scan_popc(sb, wp, W, s_wsum);
+            if (S > 0) {
+                if (tid == 0) {
+                    const unsigned long long b0 = atomicAdd(&A.stt->bump, (unsigned long long)S);
+                    if (b0 + S > A.arena_cap) atomicOr(&A.stt->arena_overflow, 1);
+                    s_base = b0;
                 }
-                if (tid == 0) A.seg_out[u] = seg_pack(b0, (uint32_t)S);
+                __syncthreads();
+                const unsigned long long b0 = s_base;
+                if (b0 + S <= A.arena_cap) {
+                    for (int c = tid; c < M; c += kLevelThreads) {
+                        const uint32_t slot = list[c];
+                        if (slot & kPrunedBit) continue;
+                        const uint32_t key = ckeys[slot];
+                        const uint32_t h = key & kHubMask;
+                        const uint32_t r = wp[h >> 5] + __popc(sb[h >> 5] & ((1u << (h & 31)) - 1u));
+                        A.hub_arena[b0 + r] = h | (key & kOvfBit);
+                        A.cnt_arena[b0 + r] = ccnt[slot];
+                    }
+                    if (tid == 0) A.seg_out[u] = seg_pack(b0, (uint32_t)S);
+                }
+            }
+        } else {
+            for (int c = tid; c < M; c += kLevelThreads) {
+                const uint32_t slot = list[c];
+                if (!(slot & kPrunedBit))
+                    sortbuf[atomicAdd(&s_nsurv, 1)] = ((unsigned long long)(ckeys[slot] & kHubMask) << 32) | slot;
+            }
+            __syncthreads();
+            const int S = s_nsurv;
+            if (S > 0) {
+                const uint32_t P = pow2_ceil((uint64_t)S);
+                for (uint32_t i = S + tid; i < P; i += kLevelThreads) sortbuf[i] = ~0ull;
+                __syncthreads();
+                block_bitonic_sort(sortbuf, P);
+                if (tid == 0) {
+                    const unsigned long long b0 = atomicAdd(&A.stt->bump, (unsigned long long)S);
+                    if (b0 + S > A.arena_cap) atomicOr(&A.stt->arena_overflow, 1);
+                    s_base = b0;
+                }
+                __syncthreads();
+                const unsigned long long b0 = s_base;
+                if (b0 + S <= A.arena_cap) {
+                    for (int i = tid; i < S; i += kLevelThreads) {
+                        const uint32_t slot = (uint32_t)sortbuf[i];
+                        const uint32_t key = ckeys[slot];
+                        A.hub_arena[b0 + i] = (key & kHubMask) | (key & kOvfBit);
+                        A.cnt_arena[b0 + i] = ccnt[slot];
+                    }
+                    if (tid == 0) A.seg_out[u] = seg_pack(b0, (uint32_t)S);
+                }
             }
         }
         if (tid == 0) atomicAdd(&A.stt->unique_total, (unsigned long long)s_nkeys);

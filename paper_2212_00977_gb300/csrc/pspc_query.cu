@@ -16,9 +16,13 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "pspc_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pspc {
 
@@ -46,10 +50,12 @@ __device__ __forceinline__ void add_term(uint64_t& sum, uint32_t& flag, uint64_t
     sum = s;
 }
 
+template <int G>
 __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (kQueryThreads / 32);
-    for (int64_t p = ((int64_t)blockIdx.x * kQueryThreads + threadIdx.x) >> 5; p < Q.q; p += warps) {
+    auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+    const int lane = tile.thread_rank();
+    const int64_t ngroups = (int64_t)gridDim.x * (kQueryThreads / G);
+    for (int64_t p = ((int64_t)blockIdx.x * kQueryThreads + threadIdx.x) / G; p < Q.q; p += ngroups) {
         const int32_t s = __ldg(Q.pairs + 2 * p), t = __ldg(Q.pairs + 2 * p + 1);
         if (s < 0 || s >= Q.n || t < 0 || t >= Q.n) {
             if (lane == 0) {
@@ -81,19 +87,19 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
             const uint32_t ha = va ? (uint32_t)__ldg(Q.hub + ia + lane) : kNoHub;
             const uint32_t hb = vb ? (uint32_t)__ldg(Q.hub + ib + lane) : kNoHub;
             const uint16_t db = vb ? __ldg(Q.dist + ib + lane) : 0;
-            const int la = ea - ia > 32 ? 31 : (int)(ea - ia - 1);
-            const int lb = eb - ib > 32 ? 31 : (int)(eb - ib - 1);
-            const uint32_t amax = __shfl_sync(0xFFFFFFFFu, ha, la);
-            const uint32_t bmax = __shfl_sync(0xFFFFFFFFu, hb, lb);
+            const int la = ea - ia > G ? G - 1 : (int)(ea - ia - 1);
+            const int lb = eb - ib > G ? G - 1 : (int)(eb - ib - 1);
+            const uint32_t amax = tile.shfl(ha, la);
+            const uint32_t bmax = tile.shfl(hb, lb);
             // largest j with hb_j <= ha (hb is ascending over the lanes)
             int j = 0;
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const uint32_t v = __shfl_sync(0xFFFFFFFFu, hb, j + step);
+            for (int step = G / 2; step > 0; step >>= 1) {
+                const uint32_t v = tile.shfl(hb, j + step);
                 if (v <= ha) j += step;
             }
-            const uint32_t hj = __shfl_sync(0xFFFFFFFFu, hb, j);
-            const uint16_t dj = __shfl_sync(0xFFFFFFFFu, db, j);
+            const uint32_t hj = tile.shfl(hb, j);
+            const uint16_t dj = tile.shfl(db, j);
             if (va && hj == ha) {
                 const uint16_t da = __ldg(Q.dist + ia + lane);
                 const uint32_t dsum = (uint32_t)(da & 0x7FFF) + (uint32_t)(dj & 0x7FFF);
@@ -101,7 +107,8 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
                     const uint64_t ca = __ldg((const unsigned long long*)Q.cnt + ia + lane);
                     const uint64_t cb = __ldg((const unsigned long long*)Q.cnt + ib + j);
                     const uint64_t lo = ca * cb;
-                    const uint32_t tf = (uint32_t)(da >> 15) | (uint32_t)(dj >> 15) | (uint32_t)(__umul64hi(ca, cb) != 0);
+                    const uint32_t tf =
+                        (uint32_t)(da >> 15) | (uint32_t)(dj >> 15) | (uint32_t)(__umul64hi(ca, cb) != 0);
                     if (dsum < best) {
                         best = dsum;
                         sum = lo;
@@ -111,26 +118,20 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
                     }
                 }
             }
-            if (amax < bmax) {
-                ia += 32;
-            } else if (bmax < amax) {
-                ib += 32;
-            } else {
-                ia += 32;
-                ib += 32;
-            }
+            if (amax <= bmax) ia += G;
+            if (bmax <= amax) ib += G;
         }
         uint32_t gbest = best;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gbest = min(gbest, __shfl_xor_sync(0xFFFFFFFFu, gbest, o));
+        for (int o = G / 2; o > 0; o >>= 1) gbest = min(gbest, tile.shfl_xor(gbest, o));
         if (best != gbest) {
             sum = 0;
             flag = 0;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t os = __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-            const uint32_t of = __shfl_xor_sync(0xFFFFFFFFu, flag, o);
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const uint64_t os = tile.shfl_xor(sum, o);
+            const uint32_t of = tile.shfl_xor(flag, o);
             add_term(sum, flag, os, of);
         }
         if (lane == 0) {
@@ -145,6 +146,14 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
             }
         }
     }
+}
+
+// Lanes per pair: wide groups for long labels (fewer merge steps), narrow
+// groups for short ones (more pairs in flight per warp).
+static int query_group_for(const Index& ix) {
+    if (ix.query_group) return ix.query_group;
+    const double avg = ix.n ? (double)ix.entries / (double)ix.n : 0.0;
+    return avg >= 128.0 ? 32 : (avg >= 24.0 ? 16 : 8);
 }
 
 }  // namespace pspc
@@ -173,16 +182,16 @@ extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, 
     uint8_t* d_ovf = nullptr;
     int* d_err = nullptr;
     int rc = PSPC_OK;
-    cudaError_t e = cudaMallocAsync((void**)&d_err, sizeof(int), st);
+    cudaError_t e = dev_alloc((void**)&d_err, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e == cudaSuccess && !dev_in) {
-        e = cudaMallocAsync((void**)&d_pairs, (size_t)q * 8, st);
+        e = dev_alloc((void**)&d_pairs, (size_t)q * 8, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_pairs, pairs, (size_t)q * 8, cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess && !dev_out) {
-        e = cudaMallocAsync((void**)&d_dist, (size_t)q * 2, st);
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_cnt, (size_t)q * 8, st);
-        if (e == cudaSuccess && overflow) e = cudaMallocAsync((void**)&d_ovf, (size_t)q, st);
+        e = dev_alloc((void**)&d_dist, (size_t)q * 2, st);
+        if (e == cudaSuccess) e = dev_alloc((void**)&d_cnt, (size_t)q * 8, st);
+        if (e == cudaSuccess && overflow) e = dev_alloc((void**)&d_ovf, (size_t)q, st);
     }
     if (e == cudaSuccess) {
         QueryArgs Q;
@@ -198,12 +207,17 @@ extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, 
         Q.out_cnt = dev_out ? count : d_cnt;
         Q.out_ovf = dev_out ? overflow : d_ovf;
         Q.err = d_err;
+        const int G = query_group_for(ix);
+        const void* fn = G == 8 ? (const void*)k_query<8> : (G == 16 ? (const void*)k_query<16> : (const void*)k_query<32>);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_query, kQueryThreads, 0);
-        const int64_t want = (q + kQueryThreads / 32 - 1) / (kQueryThreads / 32);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQueryThreads, 0);
+        const int64_t per_block = kQueryThreads / G;
+        const int64_t want = (q + per_block - 1) / per_block;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
-        k_query<<<grid, kQueryThreads, 0, st>>>(Q);
+        if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
+        else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
+        else k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && !dev_out) {
@@ -216,11 +230,17 @@ extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_status(e);
     else if (herr) rc = PSPC_E_INVAL;
-    if (d_pairs) cudaFreeAsync(d_pairs, st);
-    if (d_dist) cudaFreeAsync(d_dist, st);
-    if (d_cnt) cudaFreeAsync(d_cnt, st);
-    if (d_ovf) cudaFreeAsync(d_ovf, st);
-    if (d_err) cudaFreeAsync(d_err, st);
+    dev_free(d_pairs, st);
+    dev_free(d_dist, st);
+    dev_free(d_cnt, st);
+    dev_free(d_ovf, st);
+    dev_free(d_err, st);
     if (prev != ix.device) cudaSetDevice(prev);
     return rc;
+}
+
+extern "C" int pspc_set_query_group(pspc_index* h, int32_t lanes) {
+    if (!h || !(lanes == 0 || lanes == 8 || lanes == 16 || lanes == 32)) return PSPC_E_INVAL;
+    h->ix.query_group = lanes;
+    return PSPC_OK;
 }

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "pspc_internal.cuh"
@@ -22,6 +23,38 @@ bool is_device_ptr(const void* p) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64];
+static bool g_pool_ok[64];
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool_ok[dev]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pools[dev], &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+            g_pool_ok[dev] = true;
+        }
+    }
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, g_pools[dev], st);
+}
+
+void dev_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
 }
 
 int cuda_status(cudaError_t e) {
@@ -93,7 +126,7 @@ static int scan_rec(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches) {
         return cuda_status(cudaGetLastError());
     }
     int64_t* sums = nullptr;
-    PSPC_TRY_CUDA(cudaMallocAsync(&sums, (size_t)tiles * sizeof(int64_t), st));
+    PSPC_TRY_CUDA(dev_alloc((void**)&sums, (size_t)tiles * sizeof(int64_t), st));
     k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(a, n, sums);
     int rc = cuda_status(cudaGetLastError());
     if (rc == PSPC_OK) rc = scan_rec(sums, tiles, st, launches);
@@ -102,7 +135,7 @@ static int scan_rec(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches) {
         rc = cuda_status(cudaGetLastError());
     }
     if (launches) *launches += 2;
-    cudaFreeAsync(sums, st);
+    dev_free(sums, st);
     return rc;
 }
 
@@ -133,12 +166,15 @@ extern "C" void pspc_free(pspc_index* h) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ix.device);
-    cudaFree(ix.rank);
-    cudaFree(ix.order);
-    cudaFree(ix.off);
-    cudaFree(ix.hub);
-    cudaFree(ix.dist);
-    cudaFree(ix.cnt);
+    // The index is only freed once no work on it is pending (every call
+    // that uses it returns after its stream has drained).
+    dev_free(ix.rank, 0);
+    dev_free(ix.order, 0);
+    dev_free(ix.off, 0);
+    dev_free(ix.hub, 0);
+    dev_free(ix.dist, 0);
+    dev_free(ix.cnt, 0);
+    cudaStreamSynchronize(0);
     cudaSetDevice(prev);
     delete h;
 }

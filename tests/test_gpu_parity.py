@@ -269,3 +269,19 @@ def test_rmat16_full_size(pspc):
     assert _check_sampled_queries(ix, g, pairs) >= 1000
     st = ix.stats()
     assert st["entries"] == len(hub)
+
+
+def test_query_group_invariance(pspc):
+    """Answers do not depend on how many lanes merge-join one pair."""
+    for name in ("ba2000", "grid32"):
+        g, rank, pairs_fn = P.workload(name)
+        ref = oracle.OracleIndex(g, rank)
+        ix = gpu_index(pspc, g, rank)
+        pairs = pairs_fn(100000)
+        rd, rc, rf, _ = ref.query(pairs)
+        for lanes in (8, 16, 32, 0):
+            ix.set_query_group(lanes)
+            d, c, f = gpu_query(ix, pairs)
+            assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
+        with pytest.raises(pspc.PSPCError):
+            ix.set_query_group(12)
