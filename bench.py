@@ -240,7 +240,7 @@ def run_ours(args):
     query_ms = [r[1] for r in res]
     st = res[-1][2]
     entries = st["entries"]
-    launches_per_step = st["kernel_launches"] + 1
+    launches_per_step = st["kernel_launches"] + st["query_kernel_launches"]
     T_build = sum(build_ms)
     T_query = sum(query_ms)
     T_step = T_build + T_query

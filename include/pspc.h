@@ -96,6 +96,8 @@ typedef struct {
     int64_t index_bytes; /* device bytes held by the finished index */
     int64_t overflow_entries; /* entries whose exact count is >= 2^64 */
     int64_t kernel_launches; /* CUDA kernels launched by pspc_build */
+    int64_t query_kernel_launches; /* CUDA kernels launched by all pspc_query
+                                      calls on this index so far */
     float build_ms;      /* device time of pspc_build, input checks included */
 } pspc_stats_t;
 
@@ -164,9 +166,11 @@ int pspc_level_stats(const pspc_index* ix, pspc_level_stat_t* out, int32_t cap,
                      int32_t* levels);
 
 /*
- * pspc_set_query_group -- tuning hook for pspc_query: the number of lanes
- * that merge-join one pair (8, 16 or 32; 0 = chosen from the average label
- * size). Results do not depend on it. Errors: PSPC_E_INVAL.
+ * pspc_set_query_group -- tuning hook for pspc_query: how one pair is
+ * merge-joined. 8, 16 or 32 = that many lanes compare 32-bit hub words held
+ * in registers; 64, 128 or 256 = one warp stages chunks of that many
+ * entries of both labels in shared memory; 0 = chosen from the average
+ * label size. Results do not depend on it. Errors: PSPC_E_INVAL.
  */
 int pspc_set_query_group(pspc_index* ix, int32_t lanes);
 

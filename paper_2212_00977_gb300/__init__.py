@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("arcs", ctypes.c_int64), ("entries", ctypes.c_int64),
                 ("levels", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("index_bytes", ctypes.c_int64), ("overflow_entries", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("build_ms", ctypes.c_float)]
+                ("kernel_launches", ctypes.c_int64), ("query_kernel_launches", ctypes.c_int64),
+                ("build_ms", ctypes.c_float)]
 
 
 # Every symbol include/pspc.h declares, with its ctypes signature.

@@ -418,14 +418,21 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         const int M = s_m;
 
         // 3a. d = 3: rule 2 asks for a common neighbour x of u and h ranked
-        // above h (x in L_1(u) and x in L_1(h)). Mark every h in (x, u) adjacent
-        // to some x in L_1(u) -- a range of x's sorted row -- then test each
-        // candidate with one bit instead of scanning L_1(h).
+        // above h (x in L_1(u) and x in L_1(h)). Walk, for every x in L_1(u),
+        // the range (x, u) of x's sorted row; a hub met there that is a
+        // candidate (bitmap cand_bm) is marked pruned (bitmap mk). This replaces
+        // scanning L_1(h) for every candidate h.
         bool marked = false;
         const uint32_t Wm = (uint32_t)((u + 31) >> 5);
-        if (d == 3 && (size_t)Wm * 4 <= (size_t)(L.list - L.map) && M > 0) {
-            uint32_t* mk = (uint32_t*)mapr;
-            for (uint32_t i = tid; i < Wm; i += kLevelThreads) mk[i] = 0u;
+        if (d == 3 && (size_t)Wm * 8 <= (size_t)(L.list - L.map) && M > 0) {
+            uint32_t* cand_bm = (uint32_t*)mapr;
+            uint32_t* mk = cand_bm + Wm;
+            for (uint32_t i = tid; i < 2 * Wm; i += kLevelThreads) cand_bm[i] = 0u;
+            __syncthreads();
+            for (int c = tid; c < M; c += kLevelThreads) {
+                const uint32_t h = ckeys[list[c]] & kHubMask;
+                atomicOr(&cand_bm[h >> 5], 1u << (h & 31));
+            }
             const uint64_t s1 = __ldg(A.seg + n + u);
             const uint32_t len1 = seg_len(s1);
             const uint32_t* xs = A.hub_arena + seg_start(s1);
@@ -471,7 +478,10 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                     }
 #pragma unroll
                     for (int t = 0; t < kGatherUnroll; ++t)
-                        if (hv[t] >= 0) atomicOr(&mk[hv[t] >> 5], 1u << (hv[t] & 31));
+                        if (hv[t] >= 0) {
+                            const uint32_t bit = 1u << (hv[t] & 31);
+                            if (cand_bm[hv[t] >> 5] & bit) atomicOr(&mk[hv[t] >> 5], bit);
+                        }
                 }
                 __syncthreads();
             }

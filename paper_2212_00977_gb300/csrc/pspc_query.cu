@@ -37,6 +37,7 @@ struct QueryArgs {
     const uint16_t* dist;
     const uint64_t* cnt;
     const int32_t* pairs;
+    const int32_t* perm;  // processing order of the pairs (grouped by source), or NULL
     int64_t q;
     uint16_t* out_dist;
     uint64_t* out_cnt;
@@ -55,7 +56,8 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
     auto tile = cg::tiled_partition<G>(cg::this_thread_block());
     const int lane = tile.thread_rank();
     const int64_t ngroups = (int64_t)gridDim.x * (kQueryThreads / G);
-    for (int64_t p = ((int64_t)blockIdx.x * kQueryThreads + threadIdx.x) / G; p < Q.q; p += ngroups) {
+    for (int64_t k = ((int64_t)blockIdx.x * kQueryThreads + threadIdx.x) / G; k < Q.q; k += ngroups) {
+        const int64_t p = Q.perm ? (int64_t)__ldg(Q.perm + k) : k;
         const int32_t s = __ldg(Q.pairs + 2 * p), t = __ldg(Q.pairs + 2 * p + 1);
         if (s < 0 || s >= Q.n || t < 0 || t >= Q.n) {
             if (lane == 0) {
@@ -148,22 +150,166 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
     }
 }
 
+// Warp per pair over chunks of CH entries staged in the warp's slice of
+// shared memory (one load round trip per chunk instead of one per 32
+// entries). Each lane looks up its A hubs in the B chunk by binary search;
+// the side whose last hub is smaller advances, and only that side is
+// reloaded.
+constexpr int kChunkWarps = kQueryThreads / 32;
+
+template <int CH>
+__global__ void __launch_bounds__(kQueryThreads) k_query_chunked(const QueryArgs Q) {
+    __shared__ uint32_t s_ha[kChunkWarps][CH], s_hb[kChunkWarps][CH];
+    __shared__ uint16_t s_da[kChunkWarps][CH], s_db[kChunkWarps][CH];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t* ha_s = s_ha[w];
+    uint32_t* hb_s = s_hb[w];
+    uint16_t* da_s = s_da[w];
+    uint16_t* db_s = s_db[w];
+    const int64_t nwarps = (int64_t)gridDim.x * kChunkWarps;
+    for (int64_t k = (int64_t)blockIdx.x * kChunkWarps + w; k < Q.q; k += nwarps) {
+        const int64_t p = Q.perm ? (int64_t)__ldg(Q.perm + k) : k;
+        const int32_t s = __ldg(Q.pairs + 2 * p), t = __ldg(Q.pairs + 2 * p + 1);
+        if (s < 0 || s >= Q.n || t < 0 || t >= Q.n) {
+            if (lane == 0) {
+                atomicOr(Q.err, 1);
+                Q.out_dist[p] = PSPC_UNREACHED;
+                Q.out_cnt[p] = 0;
+                if (Q.out_ovf) Q.out_ovf[p] = 0;
+            }
+            continue;
+        }
+        if (s == t) {
+            if (lane == 0) {
+                Q.out_dist[p] = 0;
+                Q.out_cnt[p] = 1;
+                if (Q.out_ovf) Q.out_ovf[p] = 0;
+            }
+            continue;
+        }
+        const int32_t rs = __ldg(Q.rank + s), rt = __ldg(Q.rank + t);
+        int64_t ia = __ldg(Q.off + rs);
+        const int64_t ea = __ldg(Q.off + rs + 1);
+        int64_t ib = __ldg(Q.off + rt);
+        const int64_t eb = __ldg(Q.off + rt + 1);
+        uint32_t best = 0xFFFFFFFFu;
+        uint64_t sum = 0;
+        uint32_t flag = 0;
+        bool load_a = true, load_b = true;
+        while (ia < ea && ib < eb) {
+            const int na = ea - ia < CH ? (int)(ea - ia) : CH;
+            const int nb = eb - ib < CH ? (int)(eb - ib) : CH;
+            if (load_a)
+                for (int i = lane; i < CH; i += 32) {
+                    ha_s[i] = i < na ? (uint32_t)__ldg(Q.hub + ia + i) : kNoHub;
+                    da_s[i] = i < na ? __ldg(Q.dist + ia + i) : (uint16_t)0;
+                }
+            if (load_b)
+                for (int i = lane; i < CH; i += 32) {
+                    hb_s[i] = i < nb ? (uint32_t)__ldg(Q.hub + ib + i) : kNoHub;
+                    db_s[i] = i < nb ? __ldg(Q.dist + ib + i) : (uint16_t)0;
+                }
+            __syncwarp();
+            const uint32_t amax = ha_s[na - 1], bmax = hb_s[nb - 1];
+#pragma unroll
+            for (int r = 0; r < CH / 32; ++r) {
+                const int i = lane + 32 * r;
+                const uint32_t ha = ha_s[i];
+                if (i >= na || ha > bmax) continue;
+                int lo = 0, hi = nb;  // first B hub >= ha
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (hb_s[mid] < ha) lo = mid + 1; else hi = mid;
+                }
+                if (lo < nb && hb_s[lo] == ha) {
+                    const uint16_t da = da_s[i], dbv = db_s[lo];
+                    const uint32_t dsum = (uint32_t)(da & 0x7FFF) + (uint32_t)(dbv & 0x7FFF);
+                    if (dsum <= best) {
+                        const uint64_t ca = __ldg((const unsigned long long*)Q.cnt + ia + i);
+                        const uint64_t cb = __ldg((const unsigned long long*)Q.cnt + ib + lo);
+                        const uint64_t prod = ca * cb;
+                        const uint32_t tf =
+                            (uint32_t)(da >> 15) | (uint32_t)(dbv >> 15) | (uint32_t)(__umul64hi(ca, cb) != 0);
+                        if (dsum < best) {
+                            best = dsum;
+                            sum = prod;
+                            flag = tf;
+                        } else {
+                            add_term(sum, flag, prod, tf);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            load_a = amax <= bmax;
+            load_b = bmax <= amax;
+            if (load_a) ia += na;
+            if (load_b) ib += nb;
+        }
+        uint32_t gbest = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gbest = min(gbest, __shfl_xor_sync(0xFFFFFFFFu, gbest, o));
+        if (best != gbest) {
+            sum = 0;
+            flag = 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t os = __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            const uint32_t of = __shfl_xor_sync(0xFFFFFFFFu, flag, o);
+            add_term(sum, flag, os, of);
+        }
+        if (lane == 0) {
+            if (gbest == 0xFFFFFFFFu) {
+                Q.out_dist[p] = PSPC_UNREACHED;
+                Q.out_cnt[p] = 0;
+                if (Q.out_ovf) Q.out_ovf[p] = 0;
+            } else {
+                Q.out_dist[p] = (uint16_t)gbest;
+                Q.out_cnt[p] = sum;
+                if (Q.out_ovf) Q.out_ovf[p] = (uint8_t)(flag != 0);
+            }
+        }
+    }
+}
+
+// Grouping by source: a counting sort of the pair indices by s, so that the
+// pairs sharing a source run back to back and reuse L(s) from cache. Ids
+// outside [0, n) go to an extra bucket n (they are rejected later).
+__global__ void k_pair_hist(const int32_t* __restrict__ pairs, int64_t q, int64_t n,
+                            unsigned long long* __restrict__ cnt) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= q) return;
+    const int32_t s = pairs[2 * p];
+    atomicAdd(cnt + ((s >= 0 && s < n) ? s : n), 1ull);
+}
+
+__global__ void k_pair_scatter(const int32_t* __restrict__ pairs, int64_t q, int64_t n,
+                               unsigned long long* __restrict__ pos, int32_t* __restrict__ perm) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= q) return;
+    const int32_t s = pairs[2 * p];
+    perm[atomicAdd(pos + ((s >= 0 && s < n) ? s : n), 1ull)] = (int32_t)p;
+}
+
 // Lanes per pair: wide groups for long labels (fewer merge steps), narrow
 // groups for short ones (more pairs in flight per warp).
+// Long labels: warp-staged chunks of 256 entries.
 static int query_group_for(const Index& ix) {
     if (ix.query_group) return ix.query_group;
     const double avg = ix.n ? (double)ix.entries / (double)ix.n : 0.0;
-    return avg >= 128.0 ? 32 : (avg >= 24.0 ? 16 : 8);
+    return avg >= 128.0 ? 256 : (avg >= 24.0 ? 16 : 8);
 }
 
 }  // namespace pspc
 
 using namespace pspc;
 
-extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, uint16_t* dist, uint64_t* count,
+extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q, uint16_t* dist, uint64_t* count,
                           uint8_t* overflow, void* stream) {
-    if (!h || q < 0) return PSPC_E_INVAL;
+    if (!hc || q < 0) return PSPC_E_INVAL;
     if (q == 0) return PSPC_OK;
+    pspc_index* h = const_cast<pspc_index*>(hc);  // only the launch counter changes
     if (!pairs || !dist || !count) return PSPC_E_INVAL;
     const Index& ix = h->ix;
     cudaStream_t st = (cudaStream_t)stream;
@@ -193,8 +339,30 @@ extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, 
         if (e == cudaSuccess) e = dev_alloc((void**)&d_cnt, (size_t)q * 8, st);
         if (e == cudaSuccess && overflow) e = dev_alloc((void**)&d_ovf, (size_t)q, st);
     }
-    if (e == cudaSuccess) {
+    // Group by source when sources repeat enough for L(s) to be reused.
+    int32_t* d_perm = nullptr;
+    int64_t* d_bins = nullptr;
+    const bool group = q >= 4096 && q >= ix.n / 4 && q < ((int64_t)1 << 31);
+    if (e == cudaSuccess && group) {
+        const int32_t* pin = dev_in ? pairs : d_pairs;
+        e = dev_alloc((void**)&d_perm, (size_t)q * 4, st);
+        if (e == cudaSuccess) e = dev_alloc((void**)&d_bins, (size_t)(ix.n + 2) * 8, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_bins, 0, (size_t)(ix.n + 2) * 8, st);
+        if (e == cudaSuccess) {
+            k_pair_hist<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pin, q, ix.n, (unsigned long long*)d_bins);
+            h->ix.query_launches += 2;
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) rc = exclusive_scan_i64(d_bins, ix.n + 1, st, &h->ix.query_launches);
+        if (e == cudaSuccess && rc == PSPC_OK) {
+            k_pair_scatter<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pin, q, ix.n, (unsigned long long*)d_bins,
+                                                                       d_perm);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess && rc == PSPC_OK) {
         QueryArgs Q;
+        Q.perm = d_perm;
         Q.n = ix.n;
         Q.rank = ix.rank;
         Q.off = ix.off;
@@ -208,16 +376,25 @@ extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, 
         Q.out_ovf = dev_out ? overflow : d_ovf;
         Q.err = d_err;
         const int G = query_group_for(ix);
-        const void* fn = G == 8 ? (const void*)k_query<8> : (G == 16 ? (const void*)k_query<16> : (const void*)k_query<32>);
+        const void* fn = G == 8 ? (const void*)k_query<8>
+                         : G == 16 ? (const void*)k_query<16>
+                         : G == 32 ? (const void*)k_query<32>
+                         : G == 64 ? (const void*)k_query_chunked<64>
+                         : G == 128 ? (const void*)k_query_chunked<128>
+                                    : (const void*)k_query_chunked<256>;
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQueryThreads, 0);
-        const int64_t per_block = kQueryThreads / G;
+        const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
         const int64_t want = (q + per_block - 1) / per_block;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
+        h->ix.query_launches += 1;
         if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
         else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
-        else k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
+        else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
+        else if (G == 64) k_query_chunked<64><<<grid, kQueryThreads, 0, st>>>(Q);
+        else if (G == 128) k_query_chunked<128><<<grid, kQueryThreads, 0, st>>>(Q);
+        else k_query_chunked<256><<<grid, kQueryThreads, 0, st>>>(Q);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && !dev_out) {
@@ -229,7 +406,9 @@ extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_status(e);
-    else if (herr) rc = PSPC_E_INVAL;
+    else if (herr && rc == PSPC_OK) rc = PSPC_E_INVAL;
+    dev_free(d_perm, st);
+    dev_free(d_bins, st);
     dev_free(d_pairs, st);
     dev_free(d_dist, st);
     dev_free(d_cnt, st);
@@ -240,7 +419,9 @@ extern "C" int pspc_query(const pspc_index* h, const int32_t* pairs, int64_t q, 
 }
 
 extern "C" int pspc_set_query_group(pspc_index* h, int32_t lanes) {
-    if (!h || !(lanes == 0 || lanes == 8 || lanes == 16 || lanes == 32)) return PSPC_E_INVAL;
+    if (!h || !(lanes == 0 || lanes == 8 || lanes == 16 || lanes == 32 || lanes == 64 || lanes == 128 ||
+                lanes == 256))
+        return PSPC_E_INVAL;
     h->ix.query_group = lanes;
     return PSPC_OK;
 }

@@ -191,6 +191,7 @@ extern "C" int pspc_stats(const pspc_index* h, pspc_stats_t* s) {
     s->index_bytes = (ix.n * 2 + (ix.n + 1) * 2) * 4 + ix.entries * (4 + 2 + 8);
     s->overflow_entries = ix.overflow_entries;
     s->kernel_launches = ix.launches;
+    s->query_kernel_launches = ix.query_launches;
     s->build_ms = ix.build_ms;
     return PSPC_OK;
 }

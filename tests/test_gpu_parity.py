@@ -279,7 +279,7 @@ def test_query_group_invariance(pspc):
         ix = gpu_index(pspc, g, rank)
         pairs = pairs_fn(100000)
         rd, rc, rf, _ = ref.query(pairs)
-        for lanes in (8, 16, 32, 0):
+        for lanes in (8, 16, 32, 64, 128, 256, 0):
             ix.set_query_group(lanes)
             d, c, f = gpu_query(ix, pairs)
             assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
