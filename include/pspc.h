@@ -174,6 +174,33 @@ int pspc_level_stats(const pspc_index* ix, pspc_level_stat_t* out, int32_t cap,
  */
 int pspc_set_query_group(pspc_index* ix, int32_t lanes);
 
+/*
+ * pspc_query_noalloc -- pspc_query for callers that cannot allocate device
+ * memory during a query (for example an engine whose device memory is all
+ * owned by another allocator, or a latency-critical serving loop that must
+ * never enter the driver's allocator). The paper has no counterpart: this
+ * is a deployment variant of pspc_query, with the same answers.
+ *
+ * It allocates nothing: no cudaMalloc, cudaFree or pool allocation. Its
+ * working memory (the error flag, n+2 per-source bins of 8 bytes, and q
+ * pair indices of 4 bytes, each part rounded up to 256 bytes) lives in one
+ * static device array of PSPC_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU
+ * which loads the library holds until the process exits.
+ * pairs, dist, count and overflow (may be NULL) must be device memory of
+ * the index's device; host pointers would need staging buffers and are
+ * rejected. q must satisfy 256 + round256(8*(n+2)) + 4*q <= 16 MiB
+ * (about 4.06M pairs for n = 65,536); larger q gives PSPC_E_INVAL. The
+ * first call on a device looks up the array's device address; make that
+ * first call before any stream capture. Every call shares the array and
+ * clears what it counts in; calls that overlap on the GPU (on different
+ * streams, or from different threads) race on it and must be serialized by
+ * the caller. Errors: PSPC_E_INVAL (as pspc_query, plus the size and
+ * pointer rules above), PSPC_E_CUDA.
+ */
+#define PSPC_NOALLOC_SCRATCH_BYTES (16u << 20)
+int pspc_query_noalloc(const pspc_index* ix, const int32_t* pairs, int64_t q, uint16_t* dist,
+                       uint64_t* count, uint8_t* overflow, void* stream);
+
 /* pspc_free -- release an index and all its device memory; NULL is a no-op. */
 void pspc_free(pspc_index* ix);
 

@@ -73,6 +73,7 @@ _SIGS = {
     "pspc_level_stats": (ctypes.c_int, [_P, ctypes.POINTER(LevelStat), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
     "pspc_set_query_group": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "pspc_query_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "pspc_free": (None, [_P]),
     "pspc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pspc_internal.cuh"
 
@@ -424,4 +425,165 @@ extern "C" int pspc_set_query_group(pspc_index* h, int32_t lanes) {
         return PSPC_E_INVAL;
     h->ix.query_group = lanes;
     return PSPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free queries.
+//
+// pspc_query allocates its working memory (the source-grouping permutation,
+// the per-source bins, the error flag, staging for host buffers) from the
+// library's device pool. Some callers cannot allow any device allocation
+// during a query: an engine whose device memory is entirely owned by
+// another allocator, a latency-critical serving loop that must not touch
+// the driver's allocator, or a process that has reserved all device memory
+// up front. pspc_query_noalloc answers the same queries with the same
+// kernels, but its working memory is one file-scope device array of
+// kNoallocScratchBytes that every GPU loading this library holds until the
+// process exits.
+
+namespace pspc {
+
+constexpr size_t kNoallocScratchBytes = (size_t)16 << 20;  // PSPC_NOALLOC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the host-side symbol is not a device address).
+static cudaError_t noalloc_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = (unsigned char*)g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+// Exclusive scan of a[0..m) in place, a[m] = total, by one block (1024
+// threads walking the array in tiles with a running carry).
+__global__ void __launch_bounds__(1024) k_scan_one_block(long long* a, int64_t m) {
+    __shared__ long long s_warp[32];
+    __shared__ long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < m; base += 1024) {
+        const int64_t i = base + tid;
+        const long long v = i < m ? a[i] : 0;
+        long long incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            long long t = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long u = __shfl_up_sync(0xFFFFFFFFu, t, o);
+                if (lane >= o) t += u;
+            }
+            s_warp[lane] = t;
+        }
+        __syncthreads();
+        const long long carry = s_carry;
+        if (i < m) a[i] = carry + incl - v + (warp ? s_warp[warp - 1] : 0);
+        __syncthreads();
+        if (tid == 0) s_carry = carry + s_warp[31];
+        __syncthreads();
+    }
+    if (tid == 0) a[m] = s_carry;
+}
+
+}  // namespace pspc
+
+extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, int64_t q, uint16_t* dist,
+                                  uint64_t* count, uint8_t* overflow, void* stream) {
+    if (!hc || q < 0) return PSPC_E_INVAL;
+    if (q == 0) return PSPC_OK;
+    if (!pairs || !dist || !count) return PSPC_E_INVAL;
+    pspc_index* h = const_cast<pspc_index*>(hc);  // only the launch counter changes
+    const Index& ix = h->ix;
+    // Scratch layout: error flag | n+2 source bins | q pair indices.
+    const size_t bins_off = 256;
+    const size_t perm_off = bins_off + (((size_t)(ix.n + 2) * 8 + 255) & ~(size_t)255);
+    if (perm_off + (size_t)q * 4 > kNoallocScratchBytes || q >= ((int64_t)1 << 31)) return PSPC_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != ix.device) PSPC_TRY_CUDA(cudaSetDevice(ix.device));
+    int rc = PSPC_OK;
+    if (!is_device_ptr(pairs) || !is_device_ptr(dist) || !is_device_ptr(count) ||
+        (overflow && !is_device_ptr(overflow)))
+        rc = PSPC_E_INVAL;  // host buffers would need staging memory
+    unsigned char* scratch = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (rc == PSPC_OK) e = noalloc_scratch(ix.device, &scratch);
+    if (rc == PSPC_OK && e == cudaSuccess) {
+        int* d_err = (int*)scratch;
+        long long* d_bins = (long long*)(scratch + bins_off);
+        int32_t* d_perm = (int32_t*)(scratch + perm_off);
+        // The array keeps the previous call's contents: clear what is counted.
+        e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_bins, 0, (size_t)(ix.n + 2) * 8, st);
+        if (e == cudaSuccess) {
+            k_pair_hist<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pairs, q, ix.n, (unsigned long long*)d_bins);
+            k_scan_one_block<<<1, 1024, 0, st>>>(d_bins, ix.n + 1);
+            k_pair_scatter<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pairs, q, ix.n, (unsigned long long*)d_bins,
+                                                                       d_perm);
+            h->ix.query_launches += 3;
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            QueryArgs Q;
+            Q.n = ix.n;
+            Q.rank = ix.rank;
+            Q.off = ix.off;
+            Q.hub = ix.hub;
+            Q.dist = ix.dist;
+            Q.cnt = ix.cnt;
+            Q.pairs = pairs;
+            Q.perm = d_perm;
+            Q.q = q;
+            Q.out_dist = dist;
+            Q.out_cnt = count;
+            Q.out_ovf = overflow;
+            Q.err = d_err;
+            const int G = query_group_for(ix);
+            const void* fn = G == 8 ? (const void*)k_query<8>
+                             : G == 16 ? (const void*)k_query<16>
+                             : G == 32 ? (const void*)k_query<32>
+                             : G == 64 ? (const void*)k_query_chunked<64>
+                             : G == 128 ? (const void*)k_query_chunked<128>
+                                        : (const void*)k_query_chunked<256>;
+            int sms = 0, occ = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQueryThreads, 0);
+            const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
+            const int64_t want = (q + per_block - 1) / per_block;
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
+            h->ix.query_launches += 1;
+            if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
+            else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
+            else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
+            else if (G == 64) k_query_chunked<64><<<grid, kQueryThreads, 0, st>>>(Q);
+            else if (G == 128) k_query_chunked<128><<<grid, kQueryThreads, 0, st>>>(Q);
+            else k_query_chunked<256><<<grid, kQueryThreads, 0, st>>>(Q);
+            e = cudaGetLastError();
+        }
+        int herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && herr) rc = PSPC_E_INVAL;
+    }
+    if (e != cudaSuccess) rc = cuda_status(e);
+    if (prev != ix.device) cudaSetDevice(prev);
+    return rc;
 }
