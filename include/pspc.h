@@ -73,6 +73,14 @@ typedef struct {
     int32_t max_levels;      /* stop with PSPC_E_DIST after this many levels
                                 (default 32767) */
     int32_t verbose;         /* 1: per-level line on stderr */
+    int32_t map_kind;        /* how a level tests membership in L(u):
+                                0 = automatic (bitmaps when (d-1) bitmaps
+                                of n bits fit on chip, else 3),
+                                1 = per-level bitmaps (falls back to 3 when
+                                they do not fit), 2 = on-chip hash of the
+                                label (labels that do not fit go to device
+                                scratch), 3 = binary search in the two
+                                level segments that can hold the hub */
 } pspc_opts;
 
 /* Per-level counters of the last build (level d = distance d). */
@@ -156,6 +164,26 @@ int pspc_query(const pspc_index* ix, const int32_t* pairs, int64_t q, uint16_t* 
  */
 int pspc_export(const pspc_index* ix, int64_t* off, int32_t* hub, uint16_t* dist,
                 uint64_t* cnt, uint8_t* ovf);
+
+/*
+ * pspc_export_vertices -- the labels of k selected caller vertices, gathered
+ * on the device, in the layout of pspc_export: off[k+1] (host) receives the
+ * offsets; hub/dist/cnt/ovf (host, off[k] entries) receive the entries, hubs
+ * as caller ids in hub-rank order. With hub = NULL only off is filled (to
+ * size the buffers). verts: host int32[k]. Errors: PSPC_E_INVAL (vertex out
+ * of range, NULL pointers), PSPC_E_NOMEM, PSPC_E_CUDA.
+ */
+int pspc_export_vertices(const pspc_index* ix, const int32_t* verts, int64_t k, int64_t* off,
+                         int32_t* hub, uint16_t* dist, uint64_t* cnt, uint8_t* ovf);
+
+/*
+ * pspc_hub_column -- the column of hub w (caller id): for every caller
+ * vertex v, the entry of w in L(v) -- dist[v] = sd(v,w), cnt[v] =
+ * tau(v,w) mod 2^64, ovf[v] -- or dist[v] = PSPC_UNREACHED, cnt 0, ovf 0
+ * when w is not a hub of v. Host arrays of n elements. Errors:
+ * PSPC_E_INVAL, PSPC_E_NOMEM, PSPC_E_CUDA.
+ */
+int pspc_hub_column(const pspc_index* ix, int32_t w, uint16_t* dist, uint64_t* cnt, uint8_t* ovf);
 
 /* pspc_stats -- sizes and timings of an index (host struct). */
 int pspc_stats(const pspc_index* ix, pspc_stats_t* s);

@@ -46,7 +46,7 @@ class Csr(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("cand_capacity", ctypes.c_int32), ("label_capacity", ctypes.c_int32),
                 ("arena_entries", ctypes.c_int64), ("max_levels", ctypes.c_int32),
-                ("verbose", ctypes.c_int32)]
+                ("verbose", ctypes.c_int32), ("map_kind", ctypes.c_int32)]
 
 
 class LevelStat(ctypes.Structure):
@@ -73,6 +73,8 @@ _SIGS = {
     "pspc_level_stats": (ctypes.c_int, [_P, ctypes.POINTER(LevelStat), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
     "pspc_set_query_group": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "pspc_export_vertices": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
+    "pspc_hub_column": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "pspc_query_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "pspc_free": (None, [_P]),
     "pspc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -148,7 +150,7 @@ class Index:
 
     @classmethod
     def build(cls, n: int, row_ptr, col, rank, *, stream=None, cand_capacity=0, label_capacity=0,
-              arena_entries=0, max_levels=0, verbose=False) -> "Index":
+              arena_entries=0, max_levels=0, verbose=False, map_kind=0) -> "Index":
         """pspc_build over a symmetric CSR (rows strictly ascending) and a
         rank permutation (0 = highest)."""
         lib = load()
@@ -157,7 +159,7 @@ class Index:
         _check_dtype(rank, np.int32, "rank")
         g = Csr(int(n), _ptr(row_ptr), _ptr(col))
         o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
-                 int(bool(verbose)))
+                 int(bool(verbose)), int(map_kind))
         h = _P()
         rc = lib.pspc_build(ctypes.byref(g), _ptr(rank), ctypes.byref(o), ctypes.byref(h),
                             _stream_handle(stream))
@@ -232,6 +234,36 @@ class Index:
         if rc != PSPC_OK:
             raise PSPCError(rc, "pspc_export")
         return off, hub, dist, cnt, ovf
+
+    def export_vertices(self, verts):
+        """pspc_export_vertices: labels of the given caller vertices as
+        (off, hub, dist, cnt, ovf) host arrays."""
+        lib = load()
+        v = np.ascontiguousarray(verts, dtype=np.int32)
+        k = len(v)
+        off = np.empty(k + 1, np.int64)
+        rc = lib.pspc_export_vertices(self._h, _ptr(v), k, _ptr(off), None, None, None, None)
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_export_vertices")
+        E = int(off[-1])
+        hub = np.empty(E, np.int32)
+        dist = np.empty(E, np.uint16)
+        cnt = np.empty(E, np.uint64)
+        ovf = np.empty(E, np.uint8)
+        rc = lib.pspc_export_vertices(self._h, _ptr(v), k, _ptr(off), _ptr(hub), _ptr(dist), _ptr(cnt), _ptr(ovf))
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_export_vertices")
+        return off, hub, dist, cnt, ovf
+
+    def hub_column(self, w: int):
+        """pspc_hub_column: (dist, cnt, ovf) of hub w in every label."""
+        d = np.empty(self.n, np.uint16)
+        c = np.empty(self.n, np.uint64)
+        f = np.empty(self.n, np.uint8)
+        rc = load().pspc_hub_column(self._h, int(w), _ptr(d), _ptr(c), _ptr(f))
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_hub_column")
+        return d, c, f
 
     def free(self):
         if self._h:

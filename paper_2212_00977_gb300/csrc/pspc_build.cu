@@ -733,7 +733,8 @@ struct Builder {
         if (n_off > 0) {
             const uint32_t cc = (uint32_t)std::max<unsigned long long>(hstt->need_cap_c, 64);
             const uint32_t cu = (uint32_t)std::max<unsigned long long>(hstt->need_cap_u, 64);
-            const size_t stride = (level_layout(cc, hashmap_bytes(cu)).total + 255) & ~(size_t)255;
+            const int off_kind = plan.map_kind == kMapSeg ? kMapSeg : kMapHash;
+            const size_t stride = (level_layout(cc, level_map_bytes(off_kind, d, 0, cu)).total + 255) & ~(size_t)255;
             const size_t budget = (size_t)4 << 30;
             int grid = (int)std::min<size_t>((size_t)n_off, std::max<size_t>(1, budget / stride));
             grid = std::min(grid, sms * 2);
@@ -747,7 +748,7 @@ struct Builder {
             A.gscratch = gscratch;
             A.gscratch_stride = stride;
             cudaEventRecord(ek0, st);
-            cudaError_t e = launch_level(kMapHash, true, grid, 0, A, st);
+            cudaError_t e = launch_level(off_kind, true, grid, 0, A, st);
             cudaEventRecord(ek1, st);
             out.launches += 1;
             PSPC_TRY_CUDA(e);
@@ -767,12 +768,11 @@ struct Builder {
         plan.cap_c = (uint32_t)o.cand_capacity;
         plan.cap_u = (uint32_t)o.label_capacity;
         plan.bm_words = (uint32_t)((n + 31) / 32);
-        size_t map_bytes;
-        if (bitmap_bytes(d, plan.bm_words) <= kBitmapBudget) {
+        const bool bm_fits = bitmap_bytes(d, plan.bm_words) <= kBitmapBudget;
+        if ((o.map_kind == 0 || o.map_kind == 1) && bm_fits) {
             plan.map_kind = kMapBitmap;
             plan.label_limit = INT64_MAX;
-            map_bytes = bitmap_bytes(d, plan.bm_words);
-        } else {
+        } else if (o.map_kind == 2) {
             plan.map_kind = kMapHash;
             int64_t lo = 0, hi = plan.cap_u;  // largest label size whose hash fits cap_u slots
             while (lo < hi) {
@@ -780,9 +780,11 @@ struct Builder {
                 if (label_cap_for(mid) <= plan.cap_u) lo = mid; else hi = mid - 1;
             }
             plan.label_limit = lo;
-            map_bytes = hashmap_bytes(plan.cap_u);
+        } else {
+            plan.map_kind = kMapSeg;
+            plan.label_limit = INT64_MAX;
         }
-        plan.smem_bytes = level_layout(plan.cap_c, map_bytes).total;
+        plan.smem_bytes = level_layout(plan.cap_c, level_map_bytes(plan.map_kind, d, plan.bm_words, plan.cap_u)).total;
         if (plan.smem_bytes + 1024 > (size_t)smem_optin) return PSPC_E_INVAL;  // tables must fit on chip
         PSPC_TRY_CUDA(level_kernel_attrs(plan.map_kind, plan.smem_bytes, &plan.occupancy));
         if (plan.occupancy < 1) return PSPC_E_INVAL;
@@ -1012,6 +1014,10 @@ static void fill_defaults(pspc_opts& o, const pspc_opts* user) {
     if (o.max_levels <= 0) o.max_levels = kMaxDist;
 }
 
+static bool opts_ok(const pspc_opts& o) {
+    return o.map_kind >= 0 && o.map_kind <= 3;
+}
+
 static bool pow2_in(int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
 extern "C" int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opts* opts, pspc_index** out,
@@ -1023,7 +1029,8 @@ extern "C" int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opt
     Builder B;
     B.st = (cudaStream_t)stream;
     fill_defaults(B.o, opts);
-    if (!pow2_in(B.o.cand_capacity, 1024, 16384) || !pow2_in(B.o.label_capacity, 1024, 16384)) return PSPC_E_INVAL;
+    if (!pow2_in(B.o.cand_capacity, 1024, 16384) || !pow2_in(B.o.label_capacity, 1024, 16384) || !opts_ok(B.o))
+        return PSPC_E_INVAL;
     PSPC_TRY_CUDA(cudaGetDevice(&B.dev));
     PSPC_TRY_CUDA(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, B.dev));
     cudaEvent_t t0, t1;

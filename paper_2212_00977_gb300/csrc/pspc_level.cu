@@ -167,6 +167,31 @@ struct HashMap {
     __device__ bool member(uint32_t x) const { return lookup(x) != 0xFFFFu; }
 };
 
+// No map at all: a pulled hub h can only be in L(u) at distance d-2 or d-1
+// (it is at distance d-1 from a neighbour), and a witness x in L_k(h) can
+// only be at distance d-2-k or d-1-k from u (triangle inequality with
+// sd(u,h) >= d-2). So two binary searches in u's hub-sorted level segments
+// answer every test, and nothing is built per vertex.
+struct SegMap {
+    const uint64_t* seg;
+    const uint32_t* hub_arena;
+    int64_t n, u;
+    int d;
+    __device__ bool in_level(uint32_t x, int l) const {
+        if (l < 1) return false;  // level 0 is u itself
+        const uint64_t s = __ldg(seg + (int64_t)l * n + u);
+        const uint32_t* h = hub_arena + seg_start(s);
+        uint32_t lo = 0, hi = seg_len(s);
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if ((__ldg(h + mid) & kHubMask) < x) lo = mid + 1; else hi = mid;
+        }
+        return lo < seg_len(s) && (__ldg(h + lo) & kHubMask) == x;
+    }
+    __device__ bool within(uint32_t x, int thr) const { return in_level(x, thr) || in_level(x, thr - 1); }
+    __device__ bool member(uint32_t x) const { return in_level(x, d - 1) || in_level(x, d - 2); }
+};
+
 // ---------------------------------------------------------------------------
 // Block helpers.
 
@@ -281,7 +306,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
 
     const int d = A.d;
     const int64_t n = A.n;
-    const size_t map_bytes = kMap == kMapBitmap ? bitmap_bytes(d, A.bm_words) : hashmap_bytes(A.cap_u_max);
+    const size_t map_bytes = level_map_bytes(kMap, d, A.bm_words, A.cap_u_max);
     const LevelLayout L = level_layout(A.cap_c_max, map_bytes);
     uint8_t* base = kOffChip ? A.gscratch + (size_t)blockIdx.x * A.gscratch_stride : smem;
     unsigned long long* ccnt = (unsigned long long*)(base + L.cnt);
@@ -312,7 +337,14 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
 
         BitMap bm;
         HashMap hm;
-        if (kMap == kMapBitmap) {
+        SegMap sm;
+        sm.seg = A.seg;
+        sm.hub_arena = A.hub_arena;
+        sm.n = n;
+        sm.u = u;
+        sm.d = d;
+        if (kMap == kMapSeg) {
+        } else if (kMap == kMapBitmap) {
             bm.bits = (uint32_t*)mapr;
             bm.words = A.bm_words;
             bm.d = d;
@@ -326,7 +358,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             ckeys[i] = kEmpty;
             ccnt[i] = 0ull;
         }
-        if (kMap == kMapBitmap) bm.clear(); else hm.clear();
+        if (kMap == kMapBitmap) bm.clear();
+        else if (kMap == kMapHash) hm.clear();
         if (tid == 0) {
             s_nkeys = 0;
             s_abort = 0;
@@ -337,7 +370,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         __syncthreads();
 
         // 1. label map of L_<d(u)
-        for (int l = 0; l < d; ++l) {
+        for (int l = 0; l < d && kMap != kMapSeg; ++l) {
             const uint64_t s = __ldg(A.seg + (int64_t)l * n + u);
             const uint32_t len = seg_len(s);
             const uint32_t* hs = A.hub_arena + seg_start(s);
@@ -385,7 +418,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                 for (int t = 0; t < kGatherUnroll; ++t)
                     if (ok[t]) {
                         const uint32_t h = hw[t] & kHubMask;
-                        ok[t] = !(kMap == kMapBitmap ? bm.member(h) : hm.member(h));
+                        ok[t] = !(kMap == kMapBitmap ? bm.member(h) : kMap == kMapHash ? hm.member(h) : sm.member(h));
                     }
                 uint64_t cv[kGatherUnroll];
 #pragma unroll
@@ -520,7 +553,9 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
 #pragma unroll
                         for (int t = 0; t < kProbeUnroll; ++t)
                             if (x[t] != kEmpty)
-                                hit |= kMap == kMapBitmap ? bm.within(x[t], thr) : hm.within(x[t], thr);
+                                hit |= kMap == kMapBitmap ? bm.within(x[t], thr)
+                                       : kMap == kMapHash ? hm.within(x[t], thr)
+                                                          : sm.within(x[t], thr);
                         pruned = tile.any(hit);
                     }
                 }
@@ -633,7 +668,8 @@ cudaError_t launch_cost(int d, int64_t n, int64_t arcs, const int64_t* rp, const
 
 cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy) {
     const void* f = map_kind == kMapBitmap ? (const void*)k_level<kMapBitmap, false>
-                                           : (const void*)k_level<kMapHash, false>;
+                    : map_kind == kMapHash ? (const void*)k_level<kMapHash, false>
+                                           : (const void*)k_level<kMapSeg, false>;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, f, kLevelThreads, smem_bytes);
@@ -641,12 +677,16 @@ cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy) 
 
 cudaError_t launch_level(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,
                          cudaStream_t st) {
-    if (offchip)
+    if (offchip && map_kind == kMapSeg)
+        k_level<kMapSeg, true><<<grid, kLevelThreads, 0, st>>>(A);
+    else if (offchip)
         k_level<kMapHash, true><<<grid, kLevelThreads, 0, st>>>(A);
     else if (map_kind == kMapBitmap)
         k_level<kMapBitmap, false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
-    else
+    else if (map_kind == kMapHash)
         k_level<kMapHash, false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
+    else
+        k_level<kMapSeg, false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
     return cudaGetLastError();
 }
 

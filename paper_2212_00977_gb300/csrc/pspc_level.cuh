@@ -100,7 +100,13 @@ __host__ __device__ inline uint32_t label_cap_for(int64_t lab) {
     return pow2_ceil(want < 64ull ? 64ull : want);
 }
 
-enum MapKind { kMapBitmap = 0, kMapHash = 1 };
+enum MapKind { kMapBitmap = 0, kMapHash = 1, kMapSeg = 2 };
+
+// Bytes of the label-map region for a map kind (host plan and kernel must
+// agree: the kernel carves its tables with exactly this size).
+__host__ __device__ inline size_t level_map_bytes(int kind, int d, uint32_t bm_words, uint32_t cap_u) {
+    return kind == kMapBitmap ? bitmap_bytes(d, bm_words) : kind == kMapHash ? hashmap_bytes(cap_u) : 0;
+}
 
 // Launchers (pspc_level.cu). Each returns a CUDA error code of the launch.
 cudaError_t launch_arc_src(const int64_t* rp, int64_t n, int32_t* arc_src, cudaStream_t st);

@@ -244,3 +244,174 @@ extern "C" int pspc_export(const pspc_index* h, int64_t* off, int32_t* hub, uint
     cudaSetDevice(prev);
     return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Partial extraction on the device: one hub's column, or selected labels.
+
+namespace pspc {
+
+// Thread per (rank-space) vertex: binary search of the hub in its sorted label.
+__global__ void k_hub_column(int64_t n, int32_t rw, const int32_t* __restrict__ order, const int64_t* __restrict__ off,
+                             const int32_t* __restrict__ hub, const uint16_t* __restrict__ dist,
+                             const uint64_t* __restrict__ cnt, uint16_t* out_dist, uint64_t* out_cnt,
+                             uint8_t* out_ovf) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int64_t lo = off[r], hi = off[r + 1];
+    const int64_t e = hi;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (hub[mid] < rw) lo = mid + 1; else hi = mid;
+    }
+    const int32_t v = order[r];
+    if (lo < e && hub[lo] == rw) {
+        out_dist[v] = (uint16_t)(dist[lo] & 0x7FFF);
+        out_cnt[v] = cnt[lo];
+        out_ovf[v] = (uint8_t)(dist[lo] >> 15);
+    } else {
+        out_dist[v] = PSPC_UNREACHED;
+        out_cnt[v] = 0;
+        out_ovf[v] = 0;
+    }
+}
+
+__global__ void k_vert_sizes(int64_t k, const int32_t* __restrict__ verts, int64_t n, const int32_t* __restrict__ rank,
+                             const int64_t* __restrict__ off, int64_t* __restrict__ sizes, int* err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    const int32_t v = verts[i];
+    if (v < 0 || v >= n) {
+        atomicOr(err, 1);
+        sizes[i] = 0;
+        return;
+    }
+    const int32_t r = rank[v];
+    sizes[i] = off[r + 1] - off[r];
+}
+
+// Warp per selected vertex: its label with hubs as caller ids.
+__global__ void k_vert_gather(int64_t k, const int32_t* __restrict__ verts, int64_t n, const int32_t* __restrict__ rank,
+                              const int32_t* __restrict__ order, const int64_t* __restrict__ off,
+                              const int32_t* __restrict__ hub, const uint16_t* __restrict__ dist,
+                              const uint64_t* __restrict__ cnt, const int64_t* __restrict__ pos, int32_t* o_hub,
+                              uint16_t* o_dist, uint64_t* o_cnt, uint8_t* o_ovf) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= k) return;
+    const int32_t v = verts[i];
+    if (v < 0 || v >= n) return;
+    const int32_t r = rank[v];
+    const int64_t a0 = off[r], len = off[r + 1] - a0, p0 = pos[i];
+    for (int64_t j = lane; j < len; j += 32) {
+        o_hub[p0 + j] = order[hub[a0 + j]];
+        o_dist[p0 + j] = (uint16_t)(dist[a0 + j] & 0x7FFF);
+        o_ovf[p0 + j] = (uint8_t)(dist[a0 + j] >> 15);
+        o_cnt[p0 + j] = cnt[a0 + j];
+    }
+}
+
+}  // namespace pspc
+
+extern "C" int pspc_hub_column(const pspc_index* h, int32_t w, uint16_t* dist, uint64_t* cnt, uint8_t* ovf) {
+    if (!h || !dist || !cnt || !ovf) return PSPC_E_INVAL;
+    const Index& ix = h->ix;
+    if (w < 0 || w >= ix.n) return PSPC_E_INVAL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ix.device);
+    const cudaStream_t st = 0;
+    int32_t rw = 0;
+    uint16_t* d_dist = nullptr;
+    uint64_t* d_cnt = nullptr;
+    uint8_t* d_ovf = nullptr;
+    cudaError_t e = cudaMemcpy(&rw, ix.rank + w, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = dev_alloc((void**)&d_dist, ix.n * 2, st);
+    if (e == cudaSuccess) e = dev_alloc((void**)&d_cnt, ix.n * 8, st);
+    if (e == cudaSuccess) e = dev_alloc((void**)&d_ovf, ix.n, st);
+    if (e == cudaSuccess) {
+        k_hub_column<<<(unsigned)((ix.n + 255) / 256), 256, 0, st>>>(ix.n, rw, ix.order, ix.off, ix.hub, ix.dist,
+                                                                      ix.cnt, d_dist, d_cnt, d_ovf);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dist, d_dist, ix.n * 2, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, ix.n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ovf, d_ovf, ix.n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(d_dist, st);
+    dev_free(d_cnt, st);
+    dev_free(d_ovf, st);
+    cudaStreamSynchronize(st);
+    cudaSetDevice(prev);
+    return cuda_status(e);
+}
+
+extern "C" int pspc_export_vertices(const pspc_index* h, const int32_t* verts, int64_t k, int64_t* off, int32_t* hub,
+                                    uint16_t* dist, uint64_t* cnt, uint8_t* ovf) {
+    if (!h || k < 0 || (k > 0 && !verts) || !off) return PSPC_E_INVAL;
+    const Index& ix = h->ix;
+    if (k == 0) {
+        off[0] = 0;
+        return PSPC_OK;
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ix.device);
+    const cudaStream_t st = 0;
+    int32_t* d_verts = nullptr;
+    int64_t* d_pos = nullptr;
+    int* d_err = nullptr;
+    int32_t* d_hub = nullptr;
+    uint16_t* d_dist = nullptr;
+    uint64_t* d_cnt = nullptr;
+    uint8_t* d_ovf = nullptr;
+    int herr = 0;
+    int rc = PSPC_OK;
+    cudaError_t e = dev_alloc((void**)&d_verts, k * 4, st);
+    if (e == cudaSuccess) e = dev_alloc((void**)&d_pos, (k + 1) * 8, st);
+    if (e == cudaSuccess) e = dev_alloc((void**)&d_err, 4, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_verts, verts, k * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, 4, st);
+    if (e == cudaSuccess) {
+        k_vert_sizes<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(k, d_verts, ix.n, ix.rank, ix.off, d_pos, d_err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) rc = exclusive_scan_i64(d_pos, k, st);
+    if (e == cudaSuccess && rc == PSPC_OK) e = cudaMemcpyAsync(off, d_pos, (k + 1) * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && rc == PSPC_OK) e = cudaMemcpyAsync(&herr, d_err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && rc == PSPC_OK && herr) rc = PSPC_E_INVAL;
+    // hub == NULL: only the offsets (label sizes) were asked for
+    if (e == cudaSuccess && rc == PSPC_OK && hub) {
+        if (!dist || !cnt || !ovf) {
+            rc = PSPC_E_INVAL;
+        } else {
+            const int64_t E = off[k];
+            e = dev_alloc((void**)&d_hub, E * 4, st);
+            if (e == cudaSuccess) e = dev_alloc((void**)&d_dist, E * 2, st);
+            if (e == cudaSuccess) e = dev_alloc((void**)&d_cnt, E * 8, st);
+            if (e == cudaSuccess) e = dev_alloc((void**)&d_ovf, E, st);
+            if (e == cudaSuccess) {
+                k_vert_gather<<<(unsigned)((k * 32 + 255) / 256), 256, 0, st>>>(
+                    k, d_verts, ix.n, ix.rank, ix.order, ix.off, ix.hub, ix.dist, ix.cnt, d_pos, d_hub, d_dist, d_cnt,
+                    d_ovf);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess && E) e = cudaMemcpyAsync(hub, d_hub, E * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && E) e = cudaMemcpyAsync(dist, d_dist, E * 2, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && E) e = cudaMemcpyAsync(cnt, d_cnt, E * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && E) e = cudaMemcpyAsync(ovf, d_ovf, E, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
+    }
+    dev_free(d_verts, st);
+    dev_free(d_pos, st);
+    dev_free(d_err, st);
+    dev_free(d_hub, st);
+    dev_free(d_dist, st);
+    dev_free(d_cnt, st);
+    dev_free(d_ovf, st);
+    cudaStreamSynchronize(st);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_status(e);
+    return rc;
+}

@@ -71,7 +71,8 @@ def test_paper_table(pspc):
 
 # --- small graphs against the oracle, across table capacities ---
 
-CAPS = [dict(), dict(cand_capacity=1024, label_capacity=1024)]
+CAPS = [dict(), dict(cand_capacity=1024, label_capacity=1024), dict(map_kind=2, label_capacity=1024),
+        dict(map_kind=3)]
 
 
 @pytest.mark.parametrize("seed", range(10))
@@ -168,7 +169,8 @@ def test_layout_invariance(pspc):
     pairs = pairs_fn(50000)
     outs = []
     for kw, dev in [(dict(), True), (dict(), False), (dict(cand_capacity=1024, label_capacity=1024), True),
-                    (dict(cand_capacity=8192, label_capacity=16384), True), (dict(arena_entries=1), True)]:
+                    (dict(cand_capacity=8192, label_capacity=16384), True), (dict(arena_entries=1), True),
+                    (dict(map_kind=2), True), (dict(map_kind=3), True), (dict(map_kind=2, label_capacity=1024), True)]:
         ix = gpu_index(pspc, g, rank, device=dev, **kw)
         assert_index_equal(ix, ref)
         outs.append(gpu_query(ix, pairs, device=dev))
@@ -285,3 +287,32 @@ def test_query_group_invariance(pspc):
             assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
         with pytest.raises(pspc.PSPCError):
             ix.set_query_group(12)
+
+
+@pytest.mark.parametrize("map_kind", [1, 2, 3])
+def test_grid64_every_map_kind(pspc, map_kind):
+    """Many levels and overflowing counts, under each way of testing label
+    membership."""
+    g, rank, pairs_fn = P.workload("grid64")
+    ref = oracle.OracleIndex(g, rank)
+    ix = gpu_index(pspc, g, rank, map_kind=map_kind)
+    assert_index_equal(ix, ref.export())
+
+
+def test_export_vertices_and_hub_column(pspc):
+    g, rank, _ = P.workload("ba2000")
+    ix = gpu_index(pspc, g, rank)
+    ref = oracle.OracleIndex(g, rank).export()
+    verts = np.array([5, 0, 1999, 17, 5], np.int32)
+    off, hub, dist, cnt, ovf = ix.export_vertices(verts)
+    for i, v in enumerate(verts):
+        got = [(int(hub[j]), int(dist[j]), int(cnt[j]), int(ovf[j])) for j in range(off[i], off[i + 1])]
+        assert got == ref.of(int(v))
+    for w in (0, 3, 1999):
+        d, c, f = ix.hub_column(w)
+        od, oc, of = oracle.hub_column(g, rank, w)
+        assert np.array_equal(d, od) and np.array_equal(c, oc) and np.array_equal(f, of)
+    with pytest.raises(pspc.PSPCError):
+        ix.export_vertices(np.array([2000], np.int32))
+    with pytest.raises(pspc.PSPCError):
+        ix.hub_column(-1)
