@@ -106,8 +106,17 @@ typedef struct {
     int64_t kernel_launches; /* CUDA kernels launched by pspc_build */
     int64_t query_kernel_launches; /* CUDA kernels launched by all pspc_query
                                       calls on this index so far */
+    int32_t graphs;      /* graphs the index was built from (1, or k of a batch) */
     float build_ms;      /* device time of pspc_build, input checks included */
 } pspc_stats_t;
+
+/* One graph of a batch: symmetric CSR as in pspc_csr, plus its order. */
+typedef struct {
+    int64_t n;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int32_t* rank;
+} pspc_graph;
 
 typedef struct pspc_index pspc_index;
 
@@ -138,6 +147,23 @@ int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opts* opts,
                pspc_index** out, void* stream);
 
 /*
+ * pspc_build_batch -- build the indexes of k graphs in one pass: one level
+ * loop and one set of kernel launches per level serve all of them (the
+ * batched form of pspc_build; the paper builds one graph at a time).
+ *
+ * The result is ONE index over the disjoint union of the graphs: vertex v
+ * of graph g has the id base_g + v, base_g = n_0 + ... + n_{g-1}. Each
+ * graph keeps its own order, so the labels of graph g are exactly those
+ * pspc_build gives for it alone (hubs as union ids). Queries take union ids;
+ * a pair from two different graphs is unreachable. Every graph must satisfy
+ * the rules of pspc_csr and rank; sum of n < 2^24.
+ * graphs: host array of k descriptors; their arrays may be host or device
+ * memory, borrowed for the call. Errors: as pspc_build.
+ */
+int pspc_build_batch(const pspc_graph* graphs, int32_t k, const pspc_opts* opts, pspc_index** out,
+                     void* stream);
+
+/*
  * pspc_query -- answer q SPC(s,t) queries (Eq. (1)-(2)): over the common
  * hubs h of L(s) and L(t), dist = min sd(s,h) + sd(h,t) and count = sum of
  * tau(s,h) * tau(h,t) over the hubs reaching that minimum, modulo 2^64;
@@ -154,6 +180,20 @@ int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opts* opts,
  */
 int pspc_query(const pspc_index* ix, const int32_t* pairs, int64_t q, uint16_t* dist,
                uint64_t* count, uint8_t* overflow, void* stream);
+
+/*
+ * pspc_query_async -- pspc_query in stream order, for CUDA-graph capture
+ * and pipelines: it enqueues its work on `stream` and returns without
+ * waiting, allocates nothing and never synchronises, so a capture of the
+ * stream records it. pairs, dist, count, overflow (may be NULL) and err
+ * must be device memory of the index's device, and the calling thread's
+ * current device must be the index's. *err (device int32) is cleared, then
+ * set to 1 if a pair holds a vertex id outside [0,n) (those outputs are
+ * unspecified); read it after the stream completes. Same answers as
+ * pspc_query. Errors (returned at once): PSPC_E_INVAL, PSPC_E_CUDA.
+ */
+int pspc_query_async(const pspc_index* ix, const int32_t* pairs, int64_t q, uint16_t* dist,
+                     uint64_t* count, uint8_t* overflow, int32_t* err, void* stream);
 
 /*
  * pspc_export -- copy the index to host arrays, by caller vertex id, each

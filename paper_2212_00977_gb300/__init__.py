@@ -49,6 +49,11 @@ class Opts(ctypes.Structure):
                 ("verbose", ctypes.c_int32), ("map_kind", ctypes.c_int32)]
 
 
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("rank", ctypes.c_void_p)]
+
+
 class LevelStat(ctypes.Structure):
     _fields_ = [("raw_candidates", ctypes.c_int64), ("unique_candidates", ctypes.c_int64),
                 ("entries", ctypes.c_int64), ("active_vertices", ctypes.c_int64),
@@ -60,7 +65,7 @@ class Stats(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("index_bytes", ctypes.c_int64), ("overflow_entries", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("query_kernel_launches", ctypes.c_int64),
-                ("build_ms", ctypes.c_float)]
+                ("graphs", ctypes.c_int32), ("build_ms", ctypes.c_float)]
 
 
 # Every symbol include/pspc.h declares, with its ctypes signature.
@@ -68,6 +73,9 @@ _P = ctypes.c_void_p
 _SIGS = {
     "pspc_build": (ctypes.c_int, [ctypes.POINTER(Csr), _P, ctypes.POINTER(Opts), ctypes.POINTER(_P), _P]),
     "pspc_query": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
+    "pspc_query_async": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
+    "pspc_build_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Opts),
+                                        ctypes.POINTER(_P), _P]),
     "pspc_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "pspc_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "pspc_level_stats": (ctypes.c_int, [_P, ctypes.POINTER(LevelStat), ctypes.c_int32,
@@ -166,6 +174,41 @@ class Index:
         if rc != PSPC_OK:
             raise PSPCError(rc, "pspc_build")
         return cls(h.value, int(n))
+
+    @classmethod
+    def build_batch(cls, graphs, *, stream=None, cand_capacity=0, label_capacity=0, arena_entries=0,
+                    max_levels=0, verbose=False, map_kind=0) -> "Index":
+        """pspc_build_batch over ``graphs`` = [(n, row_ptr, col, rank), ...]:
+        one index over their disjoint union (graph g's vertex v has id
+        base_g + v, base_g = sum of earlier n)."""
+        lib = load()
+        k = len(graphs)
+        arr = (GraphDesc * max(k, 1))()
+        keep = []
+        for i, (n, rp, col, rank) in enumerate(graphs):
+            _check_dtype(rp, np.int64, "row_ptr")
+            _check_dtype(col, np.int32, "col")
+            _check_dtype(rank, np.int32, "rank")
+            keep.append((rp, col, rank))
+            arr[i] = GraphDesc(int(n), _ptr(rp), _ptr(col), _ptr(rank))
+        o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
+                 int(bool(verbose)), int(map_kind))
+        h = _P()
+        rc = lib.pspc_build_batch(ctypes.cast(arr, ctypes.c_void_p), k, ctypes.byref(o), ctypes.byref(h),
+                                  _stream_handle(stream))
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_build_batch")
+        return cls(h.value, int(sum(int(g[0]) for g in graphs)))
+
+    def query_async(self, pairs, dist, count, overflow, err, *, stream=None) -> None:
+        """pspc_query_async: enqueue the queries on ``stream`` (device
+        tensors only; ``err`` a device int32 tensor of one element)."""
+        _check_dtype(pairs, np.int32, "pairs")
+        q = int(pairs.shape[0])
+        rc = load().pspc_query_async(self._h, _ptr(pairs), q, _ptr(dist), _ptr(count), _ptr(overflow), _ptr(err),
+                                     _stream_handle(stream))
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_query_async")
 
     @classmethod
     def from_graph(cls, g, rank, **kw) -> "Index":

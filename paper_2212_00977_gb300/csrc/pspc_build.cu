@@ -223,6 +223,39 @@ __global__ void k_level1_write(const int64_t* __restrict__ rp, const int32_t* __
     }
 }
 
+// Batches: the disjoint union of k graphs. Graph g's vertex v becomes
+// vbase_g + v, its arcs shift by abase_g, and its order maps to ranks
+// vbase_g + rank_g(v), so every graph keeps its own order and occupies one
+// contiguous rank range (whose start is the component base of its vertices).
+struct GraphDesc {
+    int64_t n, vbase, abase;
+    const int64_t* rp;
+    const int32_t* col;
+    const int32_t* rank;
+};
+
+__global__ void k_union(const GraphDesc* __restrict__ G, int k, int64_t N, int64_t A, int64_t* __restrict__ rp_u,
+                        int32_t* __restrict__ col_u, int32_t* __restrict__ rank_u, int32_t* __restrict__ comp_base,
+                        int* err) {
+    for (int g = blockIdx.x; g < k; g += gridDim.x) {
+        const GraphDesc d = G[g];
+        for (int64_t i = threadIdx.x; i < d.n; i += blockDim.x) {
+            rp_u[d.vbase + i] = d.rp[i] + d.abase;
+            const int32_t r = d.rank[i];
+            if (r < 0 || r >= d.n) atomicOr(err, 1);
+            rank_u[d.vbase + i] = (int32_t)(d.vbase + r);
+            comp_base[d.vbase + i] = (int32_t)d.vbase;
+        }
+        const int64_t arcs = d.rp[d.n] - d.rp[0];
+        if (d.rp[0] != 0) atomicOr(err, 1);
+        for (int64_t j = threadIdx.x; j < arcs; j += blockDim.x) {
+            const int32_t v = d.col[j];
+            col_u[d.abase + j] = (v < 0 || v >= d.n) ? -1 : (int32_t)(v + d.vbase);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rp_u[N] = A;
+}
+
 // Level 0: L_0(v) = {(v, 0, 1)}.
 __global__ void k_level0(int64_t n, uint32_t* hub_arena, uint64_t* cnt_arena, uint64_t* seg0) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -452,6 +485,8 @@ struct Builder {
     int seg_levels_cap = 0;
     uint32_t* cnt_arc = nullptr;
     int32_t* arc_src = nullptr;
+    int32_t* comp_base = nullptr;  // batches: first rank-space id of each vertex's graph
+    int64_t max_comp = 0;          // largest graph (bits per level bitmap)
     int64_t* raw_u = nullptr;
     int64_t* lab_size = nullptr;
     int32_t* items = nullptr;
@@ -480,6 +515,7 @@ struct Builder {
         dfree(seg, st);
         dfree(cnt_arc, st);
         dfree(arc_src, st);
+        dfree(comp_base, st);
         dfree(raw_u, st);
         dfree(lab_size, st);
         dfree(items, st);
@@ -506,6 +542,7 @@ struct Builder {
 
     int stage_inputs(const pspc_csr* g, const int32_t* rank_user) {
         n = g->n;
+        max_comp = n;
         if (is_device_ptr(g->row_ptr)) {
             rp = g->row_ptr;
             PSPC_TRY_CUDA(cudaMemcpyAsync(&arcs, g->row_ptr + n, 8, cudaMemcpyDeviceToHost, st));
@@ -536,8 +573,92 @@ struct Builder {
         return PSPC_OK;
     }
 
+    // Assembles the disjoint union of k graphs (host or device arrays) in
+    // device memory; rank and CSR checks then run on the union.
+    int stage_batch(const pspc_graph* graphs, int32_t k) {
+        std::vector<GraphDesc> desc(k);
+        std::vector<int64_t*> rp_tmp(k, nullptr);
+        std::vector<int32_t*> col_tmp(k, nullptr), rank_tmp(k, nullptr);
+        int64_t N = 0, A = 0;
+        int rc = PSPC_OK;
+        for (int32_t g = 0; g < k && rc == PSPC_OK; ++g) {
+            const pspc_graph& G = graphs[g];
+            if (G.n < 1 || !G.row_ptr || !G.rank) {
+                rc = PSPC_E_INVAL;
+                break;
+            }
+            int64_t arcs_g = 0;
+            const bool dev_rp = is_device_ptr(G.row_ptr);
+            if (dev_rp) {
+                cudaError_t e = cudaMemcpy(&arcs_g, G.row_ptr + G.n, 8, cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) return cuda_status(e);
+            } else {
+                arcs_g = G.row_ptr[G.n];
+            }
+            if (arcs_g < 0 || (arcs_g > 0 && !G.col)) {
+                rc = PSPC_E_INVAL;
+                break;
+            }
+            desc[g].n = G.n;
+            desc[g].vbase = N;
+            desc[g].abase = A;
+            desc[g].rp = G.row_ptr;
+            desc[g].col = G.col;
+            desc[g].rank = G.rank;
+            if (!dev_rp) {
+                PSPC_TRY_CUDA(dalloc(&rp_tmp[g], G.n + 1, st));
+                PSPC_TRY_CUDA(cudaMemcpyAsync(rp_tmp[g], G.row_ptr, (G.n + 1) * 8, cudaMemcpyHostToDevice, st));
+                desc[g].rp = rp_tmp[g];
+            }
+            if (arcs_g > 0 && !is_device_ptr(G.col)) {
+                PSPC_TRY_CUDA(dalloc(&col_tmp[g], arcs_g, st));
+                PSPC_TRY_CUDA(cudaMemcpyAsync(col_tmp[g], G.col, arcs_g * 4, cudaMemcpyHostToDevice, st));
+                desc[g].col = col_tmp[g];
+            }
+            if (!is_device_ptr(G.rank)) {
+                PSPC_TRY_CUDA(dalloc(&rank_tmp[g], G.n, st));
+                PSPC_TRY_CUDA(cudaMemcpyAsync(rank_tmp[g], G.rank, G.n * 4, cudaMemcpyHostToDevice, st));
+                desc[g].rank = rank_tmp[g];
+            }
+            N += G.n;
+            A += arcs_g;
+            max_comp = std::max(max_comp, G.n);
+            if (N > kMaxVertices || A >= ((int64_t)1 << 40)) rc = PSPC_E_INVAL;
+        }
+        if (rc == PSPC_OK) {
+            n = N;
+            arcs = A;
+            GraphDesc* d_desc = nullptr;
+            PSPC_TRY_CUDA(dalloc(&rp_in, n + 1, st));
+            PSPC_TRY_CUDA(dalloc(&col_in, arcs, st));
+            PSPC_TRY_CUDA(dalloc(&rank_in, n, st));
+            PSPC_TRY_CUDA(dalloc(&comp_base, n, st));
+            PSPC_TRY_CUDA(dalloc(&err, 1, st));
+            PSPC_TRY_CUDA(dalloc(&d_desc, k, st));
+            PSPC_TRY_CUDA(cudaMemcpyAsync(d_desc, desc.data(), k * sizeof(GraphDesc), cudaMemcpyHostToDevice, st));
+            PSPC_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+            k_union<<<std::min(k, sms * 8), 256, 0, st>>>(d_desc, k, n, arcs, rp_in, col_in, rank_in, comp_base, err);
+            out.launches += 1;
+            PSPC_TRY_CUDA(cudaGetLastError());
+            int h = 0;
+            PSPC_TRY_CUDA(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st));
+            PSPC_TRY_CUDA(cudaStreamSynchronize(st));
+            dfree(d_desc, st);
+            if (h) rc = PSPC_E_INVAL;
+            rp = rp_in;
+            col = col_in;
+            rank = rank_in;
+        }
+        for (int32_t g = 0; g < k; ++g) {
+            dfree(rp_tmp[g], st);
+            dfree(col_tmp[g], st);
+            dfree(rank_tmp[g], st);
+        }
+        return rc;
+    }
+
     int validate() {
-        PSPC_TRY_CUDA(dalloc(&err, 1, st));
+        if (!err) PSPC_TRY_CUDA(dalloc(&err, 1, st));
         PSPC_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
         uint32_t* seen = nullptr;
         PSPC_TRY_CUDA(dalloc(&seen, n, st));
@@ -707,6 +828,7 @@ struct Builder {
         A.lab_size = lab_size;
         A.stt = stt;
         A.retry_list = glist + hstt->n_global;
+        A.comp_base = comp_base;
         if (hstt->n_smem > 0) {
             A.items = items;
             A.n_items = hstt->n_smem;
@@ -767,7 +889,7 @@ struct Builder {
     int plan_level(int d, LevelPlan& plan) {
         plan.cap_c = (uint32_t)o.cand_capacity;
         plan.cap_u = (uint32_t)o.label_capacity;
-        plan.bm_words = (uint32_t)((n + 31) / 32);
+        plan.bm_words = (uint32_t)((max_comp + 31) / 32);
         const bool bm_fits = bitmap_bytes(d, plan.bm_words) <= kBitmapBudget;
         if ((o.map_kind == 0 || o.map_kind == 1) && bm_fits) {
             plan.map_kind = kMapBitmap;
@@ -1020,12 +1142,10 @@ static bool opts_ok(const pspc_opts& o) {
 
 static bool pow2_in(int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
-extern "C" int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opts* opts, pspc_index** out,
-                          void* stream) {
-    if (!out) return PSPC_E_INVAL;
-    *out = nullptr;
-    if (!g || !rank || !g->row_ptr) return PSPC_E_INVAL;
-    if (g->n < 1 || g->n > kMaxVertices) return PSPC_E_INVAL;
+// Common driver: stage the input (one graph or a batch), check it, relabel,
+// build the levels, finalize, and hand the index to the caller.
+template <typename Stage>
+static int run_build(const pspc_opts* opts, pspc_index** out, void* stream, int32_t graphs, Stage stage) {
     Builder B;
     B.st = (cudaStream_t)stream;
     fill_defaults(B.o, opts);
@@ -1037,13 +1157,14 @@ extern "C" int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opt
     PSPC_TRY_CUDA(cudaEventCreate(&t0));
     PSPC_TRY_CUDA(cudaEventCreate(&t1));
     cudaEventRecord(t0, B.st);
-    int rc = B.stage_inputs(g, rank);
+    int rc = stage(B);
     if (!rc) rc = B.validate();
     if (!rc) rc = B.relabel();
     if (!rc) {
         B.out.n = B.n;
         B.out.arcs = B.arcs;
         B.out.device = B.dev;
+        B.out.graphs = graphs;
         rc = B.build_levels();
     }
     if (!rc) rc = B.finalize();
@@ -1070,4 +1191,21 @@ extern "C" int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opt
     B.out.cnt = nullptr;
     *out = h;
     return PSPC_OK;
+}
+
+extern "C" int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opts* opts, pspc_index** out,
+                          void* stream) {
+    if (!out) return PSPC_E_INVAL;
+    *out = nullptr;
+    if (!g || !rank || !g->row_ptr) return PSPC_E_INVAL;
+    if (g->n < 1 || g->n > kMaxVertices) return PSPC_E_INVAL;
+    return run_build(opts, out, stream, 1, [&](Builder& B) { return B.stage_inputs(g, rank); });
+}
+
+extern "C" int pspc_build_batch(const pspc_graph* graphs, int32_t k, const pspc_opts* opts, pspc_index** out,
+                                void* stream) {
+    if (!out) return PSPC_E_INVAL;
+    *out = nullptr;
+    if (!graphs || k < 1) return PSPC_E_INVAL;
+    return run_build(opts, out, stream, k, [&](Builder& B) { return B.stage_batch(graphs, k); });
 }

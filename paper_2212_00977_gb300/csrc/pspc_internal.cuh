@@ -54,6 +54,7 @@ struct Index {
     int64_t launches = 0;
     int64_t query_launches = 0;  // kernels launched by pspc_query on this index
     int32_t query_group = 0;  // lanes per query pair; 0 = chosen from label sizes
+    int32_t graphs = 1;       // graphs in the batch the index was built from
     std::vector<pspc_level_stat_t> lstats;
 };
 

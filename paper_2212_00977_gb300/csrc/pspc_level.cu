@@ -120,16 +120,19 @@ struct BitMap {
     uint32_t* bits;  // (d-1) bitmaps of `words` words; bitmap j-1 = {x : d_u(x) <= j}
     uint32_t words;
     int d;
+    uint32_t base;   // first id of u's graph: bits index x - base
     __device__ void clear() const {
         const uint32_t total = (uint32_t)(d - 1) * words;
         for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) bits[i] = 0u;
     }
     __device__ void insert(uint32_t x, int l) const {
         if (l == 0) return;  // u itself is never a candidate or a witness
+        x -= base;
         const uint32_t m = 1u << (x & 31);
         for (int j = l; j <= d - 1; ++j) atomicOr(&bits[(uint32_t)(j - 1) * words + (x >> 5)], m);
     }
     __device__ bool within(uint32_t x, int thr) const {  // d_u(x) <= thr, 1 <= thr <= d-1
+        x -= base;
         return (bits[(uint32_t)(thr - 1) * words + (x >> 5)] >> (x & 31)) & 1u;
     }
     __device__ bool member(uint32_t x) const { return d > 1 && within(x, d - 1); }
@@ -329,6 +332,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         const int item = s_item;
         if (item >= A.n_items) break;
         const int64_t u = A.items[item];
+        const uint32_t cbase = A.comp_base ? (uint32_t)__ldg(A.comp_base + u) : 0u;
         const int64_t raw = A.raw_u[u];
         const uint32_t cap_c = cand_cap_for(raw, u, A.cap_c_max);
         // Off chip the table holds every distinct hub; on chip a vertex whose
@@ -347,6 +351,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         } else if (kMap == kMapBitmap) {
             bm.bits = (uint32_t*)mapr;
             bm.words = A.bm_words;
+            bm.base = cbase;
             bm.d = d;
         } else {
             hm.cap = label_cap_for(A.lab_size[u]);
@@ -456,14 +461,14 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         // candidate (bitmap cand_bm) is marked pruned (bitmap mk). This replaces
         // scanning L_1(h) for every candidate h.
         bool marked = false;
-        const uint32_t Wm = (uint32_t)((u + 31) >> 5);
+        const uint32_t Wm = (uint32_t)((u - cbase + 31) >> 5);
         if (d == 3 && (size_t)Wm * 8 <= (size_t)(L.list - L.map) && M > 0) {
             uint32_t* cand_bm = (uint32_t*)mapr;
             uint32_t* mk = cand_bm + Wm;
             for (uint32_t i = tid; i < 2 * Wm; i += kLevelThreads) cand_bm[i] = 0u;
             __syncthreads();
             for (int c = tid; c < M; c += kLevelThreads) {
-                const uint32_t h = ckeys[list[c]] & kHubMask;
+                const uint32_t h = (ckeys[list[c]] & kHubMask) - cbase;
                 atomicOr(&cand_bm[h >> 5], 1u << (h & 31));
             }
             const uint64_t s1 = __ldg(A.seg + n + u);
@@ -512,15 +517,16 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
 #pragma unroll
                     for (int t = 0; t < kGatherUnroll; ++t)
                         if (hv[t] >= 0) {
-                            const uint32_t bit = 1u << (hv[t] & 31);
-                            if (cand_bm[hv[t] >> 5] & bit) atomicOr(&mk[hv[t] >> 5], bit);
+                            const uint32_t hr = (uint32_t)hv[t] - cbase;
+                            const uint32_t bit = 1u << (hr & 31);
+                            if (cand_bm[hr >> 5] & bit) atomicOr(&mk[hr >> 5], bit);
                         }
                 }
                 __syncthreads();
             }
             for (int c = tid; c < M; c += kLevelThreads) {
                 const uint32_t slot = list[c];
-                const uint32_t h = ckeys[slot] & kHubMask;
+                const uint32_t h = (ckeys[slot] & kHubMask) - cbase;
                 if ((mk[h >> 5] >> (h & 31)) & 1u) list[c] = slot | kPrunedBit;
             }
             __syncthreads();
@@ -568,7 +574,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         // when a bitmap of u bits and its word prefix fit the map region, a
         // survivor's rank is the prefix of its word plus a popcount; else a
         // bitonic sort.
-        const uint32_t W = (uint32_t)((u + 31) >> 5);
+        const uint32_t W = (uint32_t)((u - cbase + 31) >> 5);
         const size_t region = (L.list - L.map);
         if ((size_t)W * 8 <= region) {
             uint32_t* sb = (uint32_t*)mapr;
@@ -578,7 +584,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             for (int c = tid; c < M; c += kLevelThreads) {
                 const uint32_t slot = list[c];
                 if (!(slot & kPrunedBit)) {
-                    const uint32_t h = ckeys[slot] & kHubMask;
+                    const uint32_t h = (ckeys[slot] & kHubMask) - cbase;
                     atomicOr(&sb[h >> 5], 1u << (h & 31));
                 }
             }
@@ -598,7 +604,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                         if (slot & kPrunedBit) continue;
                         const uint32_t key = ckeys[slot];
                         const uint32_t h = key & kHubMask;
-                        const uint32_t r = wp[h >> 5] + __popc(sb[h >> 5] & ((1u << (h & 31)) - 1u));
+                        const uint32_t hr = h - cbase;
+                        const uint32_t r = wp[hr >> 5] + __popc(sb[hr >> 5] & ((1u << (hr & 31)) - 1u));
                         A.hub_arena[b0 + r] = h | (key & kOvfBit);
                         A.cnt_arena[b0 + r] = ccnt[slot];
                     }

@@ -56,6 +56,7 @@ struct LevelArgs {
     uint32_t cap_c_max;   // candidate table slots (on chip, or per-CTA scratch)
     uint32_t cap_u_max;   // label hash slots (hash map kind)
     uint32_t bm_words;    // words per level bitmap (bitmap map kind)
+    const int32_t* comp_base;  // first rank-space id of each vertex's graph in a batch (NULL: 0)
     uint8_t* gscratch;    // per-CTA table memory when the tables are off chip
     size_t gscratch_stride;
 };

@@ -587,3 +587,59 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
     if (prev != ix.device) cudaSetDevice(prev);
     return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Stream-ordered queries for CUDA graphs: no host synchronisation, no
+// allocation, errors reported through a caller-provided device flag.
+
+extern "C" int pspc_query_async(const pspc_index* hc, const int32_t* pairs, int64_t q, uint16_t* dist,
+                                uint64_t* count, uint8_t* overflow, int32_t* err, void* stream) {
+    if (!hc || q < 0 || q >= ((int64_t)1 << 40)) return PSPC_E_INVAL;
+    if (q == 0) return PSPC_OK;
+    if (!pairs || !dist || !count || !err) return PSPC_E_INVAL;
+    pspc_index* h = const_cast<pspc_index*>(hc);  // only the launch counter changes
+    const Index& ix = h->ix;
+    int cur = 0;
+    PSPC_TRY_CUDA(cudaGetDevice(&cur));
+    if (cur != ix.device) return PSPC_E_INVAL;  // the stream belongs to the index's device
+    if (!is_device_ptr(pairs) || !is_device_ptr(dist) || !is_device_ptr(count) || !is_device_ptr(err) ||
+        (overflow && !is_device_ptr(overflow)))
+        return PSPC_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    PSPC_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    QueryArgs Q;
+    Q.n = ix.n;
+    Q.rank = ix.rank;
+    Q.off = ix.off;
+    Q.hub = ix.hub;
+    Q.dist = ix.dist;
+    Q.cnt = ix.cnt;
+    Q.pairs = pairs;
+    Q.perm = nullptr;
+    Q.q = q;
+    Q.out_dist = dist;
+    Q.out_cnt = count;
+    Q.out_ovf = overflow;
+    Q.err = err;
+    const int G = query_group_for(ix);
+    const void* fn = G == 8 ? (const void*)k_query<8>
+                     : G == 16 ? (const void*)k_query<16>
+                     : G == 32 ? (const void*)k_query<32>
+                     : G == 64 ? (const void*)k_query_chunked<64>
+                     : G == 128 ? (const void*)k_query_chunked<128>
+                                : (const void*)k_query_chunked<256>;
+    int sms = 0, occ = 0;
+    PSPC_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device));
+    PSPC_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQueryThreads, 0));
+    const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
+    const int64_t want = (q + per_block - 1) / per_block;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
+    h->ix.query_launches += 1;
+    if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
+    else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
+    else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
+    else if (G == 64) k_query_chunked<64><<<grid, kQueryThreads, 0, st>>>(Q);
+    else if (G == 128) k_query_chunked<128><<<grid, kQueryThreads, 0, st>>>(Q);
+    else k_query_chunked<256><<<grid, kQueryThreads, 0, st>>>(Q);
+    return cuda_status(cudaGetLastError());
+}

@@ -192,6 +192,7 @@ extern "C" int pspc_stats(const pspc_index* h, pspc_stats_t* s) {
     s->overflow_entries = ix.overflow_entries;
     s->kernel_launches = ix.launches;
     s->query_kernel_launches = ix.query_launches;
+    s->graphs = ix.graphs;
     s->build_ms = ix.build_ms;
     return PSPC_OK;
 }

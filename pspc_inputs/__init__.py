@@ -27,6 +27,7 @@ __all__ = [
     "query_pairs",
     "largest_component",
     "workload",
+    "ba_batch",
 ]
 
 
@@ -205,6 +206,37 @@ def query_pairs(n: int, q: int, seed: int) -> np.ndarray:
     """int32[q, 2] of uniform (s, t) pairs; s == t is allowed."""
     rng = np.random.default_rng(seed)
     return rng.integers(0, n, size=(q, 2), dtype=np.int64).astype(np.int32)
+
+
+def _ba_member(args):
+    i, n, m, seed = args
+    g = barabasi_albert(int(n), int(m), int(seed))
+    return i, g.n, g.row_ptr, g.col, degree_rank(g, "id")
+
+
+def ba_batch(count: int = 512, n_range=(500, 20000), m_range=(2, 8), seed: int = 1000, workers: int = 0):
+    """A batch of Barabasi-Albert graphs of uneven size: graph i has
+    n_i ~ U[n_range] and m_i ~ U{m_range} (both drawn with numpy seed
+    ``seed``), is generated with seed ``seed + i``, and is ranked by degree
+    descending (ties by id). Returns a list of (n, row_ptr, col, rank).
+    ``workers`` > 1 generates in a spawn process pool."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_range[0], n_range[1] + 1, size=count)
+    ms = rng.integers(m_range[0], m_range[1] + 1, size=count)
+    ms = np.minimum(ms, ns - 1)
+    jobs = [(i, ns[i], ms[i], seed + i) for i in range(count)]
+    out = [None] * count
+    if workers and workers > 1:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for i, n, rp, col, rank in pool.imap_unordered(_ba_member, jobs, chunksize=4):
+                out[i] = (n, rp, col, rank)
+    else:
+        for job in jobs:
+            i, n, rp, col, rank = _ba_member(job)
+            out[i] = (n, rp, col, rank)
+    return out
 
 
 RMAT_ABCD = (0.57, 0.19, 0.19, 0.05)

@@ -289,3 +289,13 @@ def test_rank_must_be_permutation():
     g = G.path(4)
     with pytest.raises(ValueError):
         oracle.OracleIndex(g, np.array([0, 1, 1, 2], np.int32))
+
+
+def test_ba_batch_is_seeded_and_pool_independent():
+    import pspc_inputs as P
+
+    a = P.ba_batch(6, n_range=(50, 300), m_range=(1, 5), seed=4)
+    b = P.ba_batch(6, n_range=(50, 300), m_range=(1, 5), seed=4, workers=2)
+    assert len(a) == 6
+    for x, y in zip(a, b):
+        assert x[0] == y[0] and all(np.array_equal(u, v) for u, v in zip(x[1:], y[1:]))
