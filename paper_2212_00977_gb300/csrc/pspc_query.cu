@@ -351,10 +351,14 @@ extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q,
         if (e == cudaSuccess) e = cudaMemsetAsync(d_bins, 0, (size_t)(ix.n + 2) * 8, st);
         if (e == cudaSuccess) {
             k_pair_hist<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pin, q, ix.n, (unsigned long long*)d_bins);
-            h->ix.query_launches += 2;
+            __atomic_fetch_add(&h->ix.query_launches, (int64_t)2, __ATOMIC_RELAXED);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) rc = exclusive_scan_i64(d_bins, ix.n + 1, st, &h->ix.query_launches);
+        if (e == cudaSuccess) {
+            int64_t scan_launches = 0;
+            rc = exclusive_scan_i64(d_bins, ix.n + 1, st, &scan_launches);
+            __atomic_fetch_add(&h->ix.query_launches, scan_launches, __ATOMIC_RELAXED);
+        }
         if (e == cudaSuccess && rc == PSPC_OK) {
             k_pair_scatter<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pin, q, ix.n, (unsigned long long*)d_bins,
                                                                        d_perm);
@@ -389,7 +393,7 @@ extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q,
         const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
         const int64_t want = (q + per_block - 1) / per_block;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
-        h->ix.query_launches += 1;
+        __atomic_fetch_add(&h->ix.query_launches, (int64_t)1, __ATOMIC_RELAXED);
         if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
         else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
         else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
@@ -538,7 +542,7 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
             k_scan_one_block<<<1, 1024, 0, st>>>(d_bins, ix.n + 1);
             k_pair_scatter<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pairs, q, ix.n, (unsigned long long*)d_bins,
                                                                        d_perm);
-            h->ix.query_launches += 3;
+            __atomic_fetch_add(&h->ix.query_launches, (int64_t)3, __ATOMIC_RELAXED);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
@@ -569,7 +573,7 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
             const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
             const int64_t want = (q + per_block - 1) / per_block;
             const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
-            h->ix.query_launches += 1;
+            __atomic_fetch_add(&h->ix.query_launches, (int64_t)1, __ATOMIC_RELAXED);
             if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
             else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
             else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
@@ -634,7 +638,7 @@ extern "C" int pspc_query_async(const pspc_index* hc, const int32_t* pairs, int6
     const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
     const int64_t want = (q + per_block - 1) / per_block;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
-    h->ix.query_launches += 1;
+    __atomic_fetch_add(&h->ix.query_launches, (int64_t)1, __ATOMIC_RELAXED);
     if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
     else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
     else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);

@@ -1,0 +1,95 @@
+"""Serving: continuously batched queries and overlapping builds give every
+request exactly the answer it gets alone."""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import pspc_inputs as P
+from tests import _graphs as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_00977_gb300 as pspc
+    from paper_2212_00977_gb300 import serve
+
+    pspc.load()
+    return torch, pspc, serve
+
+
+def test_results_same_alone_and_in_the_mix(env):
+    torch, pspc, serve = env
+    srv = serve.SPCServer(max_batch_pairs=1 << 16)
+    try:
+        ga, ra, _ = P.workload("rmat12_ef16")
+        gb, rb, _ = P.workload("ba2000")
+        A = pspc.Index.from_graph(ga, ra)
+        B = pspc.Index.from_graph(gb, rb)
+        srv.add_index("A", A)
+        srv.add_index("B", B)
+        rng = np.random.default_rng(1)
+        reqs = []
+        # builds that overlap the query traffic
+        gc = G.grid(30)
+        gd = P.barabasi_albert(3000, 3, 11)
+        bc = srv.submit_build("C", gc, G.random_rank(gc.n, 2))
+        bd = srv.submit_build("D", gd, G.degree_rank(gd))
+
+        def client(seed):
+            r2 = np.random.default_rng(seed)
+            for _ in range(60):
+                name, g = ("A", ga) if r2.random() < 0.6 else ("B", gb)
+                k = int(np.exp(r2.uniform(0, np.log(4096))))
+                pairs = r2.integers(0, g.n, size=(k, 2)).astype(np.int32)
+                reqs.append((name, pairs, srv.submit_query(name, pairs)))
+                time.sleep(r2.exponential(0.0005))
+
+        threads = [threading.Thread(target=client, args=(s,)) for s in range(4)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        bc.wait(120)
+        bd.wait(120)
+        for name, g in (("C", gc), ("D", gd)):
+            pairs = rng.integers(0, g.n, size=(3000, 2)).astype(np.int32)
+            reqs.append((name, pairs, srv.submit_query(name, pairs)))
+        # an out-of-range request fails alone, without spoiling its batch
+        bad = srv.submit_query("A", np.array([[0, ga.n]], np.int32))
+        good = srv.submit_query("A", np.array([[0, 1]], np.int32))
+        with pytest.raises(pspc.PSPCError):
+            bad.wait(60)
+        good.wait(60)
+        alone = {"A": A, "B": B, "C": srv.indexes["C"][0], "D": srv.indexes["D"][0]}
+        for name, pairs, r in reqs:
+            d, c, f = r.wait(60)
+            rd, rc, rf = alone[name].query(pairs)
+            assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
+        assert srv.batches < len(reqs)  # requests were batched
+        lat = [r.latency for _, _, r in reqs]
+        assert serve.percentile(lat, 99) < 60
+    finally:
+        srv.close()
+
+
+def test_admission_rejects_a_build_that_cannot_fit(env):
+    torch, pspc, serve = env
+    srv = serve.SPCServer(max_batch_pairs=1 << 10, memory_budget=1 << 20)
+    try:
+        g = P.barabasi_albert(5000, 4, 3)
+        r = srv.submit_build("big", g, G.degree_rank(g))
+        with pytest.raises(MemoryError):
+            r.wait(60)
+        with pytest.raises(KeyError):
+            srv.submit_query("nope", np.array([[0, 1]], np.int32)).wait(60)
+    finally:
+        srv.close()
