@@ -439,12 +439,131 @@ def run_batch(args):
     return 0 if same else 1
 
 
+def run_serve(args):
+    """Resident R-MAT scale-20 index; Poisson arrivals (mean 2,000/s) of
+    query sets sized log-uniform in [1, 4096]; 1% of the requests are builds
+    of Barabasi-Albert graphs (n ~ log-uniform [10^3, 10^5], m ~ U{2..8})
+    admitted by estimated label memory. Reports p50/p99 latency from arrival
+    to result on the host, and query throughput."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2212_00977_gb300 as pspc
+    import pspc_inputs as P
+    from paper_2212_00977_gb300 import serve
+
+    rate = 2000.0
+    duration = 8.0
+    workers = min(16, os.cpu_count() or 1)
+    rng = np.random.default_rng(4)
+    n_req = int(rate * duration * 1.2)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < duration]
+    is_build = rng.random(len(arrivals)) < 0.01
+    n_builds = int(is_build.sum())
+    bn = np.exp(rng.uniform(np.log(1e3), np.log(1e5), size=n_builds)).astype(np.int64)
+    bm = rng.integers(2, 9, size=n_builds)
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(workers) as pool:
+        built = pool.map(P._ba_member, [(i, bn[i], bm[i], 5000 + i) for i in range(n_builds)])
+    build_graphs = [(P.Graph(n, rp, col, "ba"), rank) for (_, n, rp, col, rank) in built]
+    g, rank, _ = P.workload("rmat20")
+    sizes = np.exp(rng.uniform(0, np.log(4096), size=len(arrivals))).astype(np.int64)
+    pool_pairs = P.query_pairs(g.n, int(sizes.sum()) + 1, 2)
+
+    torch.cuda.set_device(0)
+    pspc.load()
+    dev = torch.device("cuda", 0)
+    ix = pspc.Index.build(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                          torch.from_numpy(rank).to(dev))
+    srv = serve.SPCServer(max_batch_pairs=1 << 21)
+    srv.add_index("rmat20", ix)
+    # warm-up
+    srv.submit_query("rmat20", pool_pairs[:4096]).wait(60)
+    reqs_q, reqs_b = [], []
+    t0 = time.perf_counter() + 0.2
+    off = 0
+    bi = 0
+    resident_built = []
+
+    def driver():
+        nonlocal off, bi
+        for k, a in enumerate(arrivals):
+            at = t0 + a
+            now = time.perf_counter()
+            if at > now:
+                time.sleep(at - now)
+            if is_build[k]:
+                gb, rb = build_graphs[bi]
+                name = f"ba{bi}"
+                reqs_b.append((name, srv.submit_build(name, gb, rb, arrival=at)))
+                bi += 1
+            else:
+                sz = int(sizes[k])
+                reqs_q.append(srv.submit_query("rmat20", pool_pairs[off:off + sz], arrival=at))
+                off += sz
+
+    done_builds = 0
+    stop_reaper = threading.Event()
+
+    def reaper():
+        # clients release a built index as soon as it is ready
+        nonlocal done_builds
+        k = 0
+        while not (stop_reaper.is_set() and k >= len(reqs_b)):
+            if k >= len(reqs_b):
+                time.sleep(0.001)
+                continue
+            name, r = reqs_b[k]
+            try:
+                r.wait(600)
+                done_builds += 1
+                srv.drop_index(name)
+            except MemoryError:
+                pass
+            k += 1
+
+    th = threading.Thread(target=driver)
+    rp = threading.Thread(target=reaper)
+    th.start()
+    rp.start()
+    th.join()
+    for r in reqs_q:
+        r.wait(600)
+    stop_reaper.set()
+    rp.join()
+    t_end = max(r.finished for r in reqs_q)
+    srv.close()
+    lat_ms = [1e3 * r.latency for r in reqs_q]
+    blat_ms = [1e3 * r.latency for _, r in reqs_b if r.finished]
+    pairs_total = int(sum(len(r.pairs) for r in reqs_q))
+    wall = t_end - t0
+    line = {"metric": "SPC queries/s served; p50/p99 query latency", "value": pairs_total / wall,
+            "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "resident R-MAT scale 20 index; Poisson arrivals mean 2000/s for 8 s; query sets "
+                                   "log-uniform in [1,4096] pairs; 1% build requests of BA graphs n in [1e3,1e5] "
+                                   "(log-uniform), m ~ U{2..8}, admitted by estimated label memory",
+                       "requests": len(arrivals), "query_requests": len(reqs_q), "build_requests": len(reqs_b)},
+            "p50_ms": serve.percentile(lat_ms, 50), "p99_ms": serve.percentile(lat_ms, 99),
+            "p50_build_ms": serve.percentile(blat_ms, 50), "p99_build_ms": serve.percentile(blat_ms, 99),
+            "builds_done": done_builds, "batches": srv.batches, "pairs": pairs_total}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

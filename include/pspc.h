@@ -81,6 +81,13 @@ typedef struct {
                                 label (labels that do not fit go to device
                                 scratch), 3 = binary search in the two
                                 level segments that can hold the hub */
+    int32_t max_ctas;        /* cap on the CTAs of the build's persistent
+                                kernels (0 = fill the GPU) */
+    int32_t granular;        /* 1: launch the level kernel with one CTA per
+                                vertex instead of persistent CTAs, so that
+                                work on a higher-priority stream (a query
+                                batch next to a build) gets SMs as soon as
+                                any vertex finishes; same results */
 } pspc_opts;
 
 /* Per-level counters of the last build (level d = distance d). */

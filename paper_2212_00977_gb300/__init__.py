@@ -46,7 +46,8 @@ class Csr(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("cand_capacity", ctypes.c_int32), ("label_capacity", ctypes.c_int32),
                 ("arena_entries", ctypes.c_int64), ("max_levels", ctypes.c_int32),
-                ("verbose", ctypes.c_int32), ("map_kind", ctypes.c_int32)]
+                ("verbose", ctypes.c_int32), ("map_kind", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
+                ("granular", ctypes.c_int32)]
 
 
 class GraphDesc(ctypes.Structure):
@@ -158,7 +159,8 @@ class Index:
 
     @classmethod
     def build(cls, n: int, row_ptr, col, rank, *, stream=None, cand_capacity=0, label_capacity=0,
-              arena_entries=0, max_levels=0, verbose=False, map_kind=0) -> "Index":
+              arena_entries=0, max_levels=0, verbose=False, map_kind=0, max_ctas=0,
+              granular=False) -> "Index":
         """pspc_build over a symmetric CSR (rows strictly ascending) and a
         rank permutation (0 = highest)."""
         lib = load()
@@ -167,7 +169,7 @@ class Index:
         _check_dtype(rank, np.int32, "rank")
         g = Csr(int(n), _ptr(row_ptr), _ptr(col))
         o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
-                 int(bool(verbose)), int(map_kind))
+                 int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)))
         h = _P()
         rc = lib.pspc_build(ctypes.byref(g), _ptr(rank), ctypes.byref(o), ctypes.byref(h),
                             _stream_handle(stream))
@@ -177,7 +179,8 @@ class Index:
 
     @classmethod
     def build_batch(cls, graphs, *, stream=None, cand_capacity=0, label_capacity=0, arena_entries=0,
-                    max_levels=0, verbose=False, map_kind=0) -> "Index":
+                    max_levels=0, verbose=False, map_kind=0, max_ctas=0,
+              granular=False) -> "Index":
         """pspc_build_batch over ``graphs`` = [(n, row_ptr, col, rank), ...]:
         one index over their disjoint union (graph g's vertex v has id
         base_g + v, base_g = sum of earlier n)."""
@@ -192,7 +195,7 @@ class Index:
             keep.append((rp, col, rank))
             arr[i] = GraphDesc(int(n), _ptr(rp), _ptr(col), _ptr(rank))
         o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
-                 int(bool(verbose)), int(map_kind))
+                 int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)))
         h = _P()
         rc = lib.pspc_build_batch(ctypes.cast(arr, ctypes.c_void_p), k, ctypes.byref(o), ctypes.byref(h),
                                   _stream_handle(stream))

@@ -705,7 +705,8 @@ struct Builder {
         PSPC_TRY_CUDA(dalloc(&big, n, st));
         PSPC_TRY_CUDA(dalloc(&nbig, 1, st));
         PSPC_TRY_CUDA(cudaMemsetAsync(nbig, 0, sizeof(int), st));
-        const int grid = (int)std::min<int64_t>(n, (int64_t)sms * 16);
+        int grid = (int)std::min<int64_t>(n, (int64_t)sms * 16);
+        if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
         k_sort_rows<<<grid, kRowThreads, 0, st>>>(rp_r, col_r, n, big, nbig);
         out.launches += 1;
         PSPC_TRY_CUDA(cudaGetLastError());
@@ -836,7 +837,10 @@ struct Builder {
             A.cap_c_max = plan.cap_c;
             A.cap_u_max = plan.cap_u;
             A.bm_words = plan.bm_words;
-            const int grid = std::min(hstt->n_smem, sms * plan.occupancy);
+            int grid = std::min(hstt->n_smem, sms * plan.occupancy);
+            if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
+            A.granular = o.granular ? 1 : 0;
+            if (o.granular) grid = hstt->n_smem;
             cudaEventRecord(ek0, st);
             cudaError_t e = launch_level(plan.map_kind, false, grid, plan.smem_bytes, A, st);
             cudaEventRecord(ek1, st);
@@ -859,7 +863,9 @@ struct Builder {
             const size_t stride = (level_layout(cc, level_map_bytes(off_kind, d, 0, cu)).total + 255) & ~(size_t)255;
             const size_t budget = (size_t)4 << 30;
             int grid = (int)std::min<size_t>((size_t)n_off, std::max<size_t>(1, budget / stride));
-            grid = std::min(grid, sms * 2);
+            // granular builds leave every SM half free for concurrent work
+            grid = std::min(grid, o.granular ? sms : sms * 2);
+            if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
             rc = ensure_gscratch(stride * grid);
             if (rc) return rc;
             A.items = glist;
@@ -869,6 +875,7 @@ struct Builder {
             A.cap_u_max = cu;
             A.gscratch = gscratch;
             A.gscratch_stride = stride;
+            A.granular = 0;  // off-chip scratch slabs are per persistent CTA
             cudaEventRecord(ek0, st);
             cudaError_t e = launch_level(off_kind, true, grid, 0, A, st);
             cudaEventRecord(ek1, st);
@@ -979,6 +986,15 @@ struct Builder {
             if (hstt->n_active == 0) break;
             const long long raw_total = (long long)hstt->raw_total;
             const long long active_arcs = (long long)hstt->active_arcs;
+            // Size the arena for this level before running it: the level
+            // adds at most one entry per distinct pulled (u, h), bounded here
+            // by the pulled count and by four times what exists so far.
+            {
+                const unsigned long long used = lvl_base[d];
+                const unsigned long long add =
+                    std::min<unsigned long long>((unsigned long long)raw_total, 4 * used + (unsigned long long)n);
+                if (used + add > arena_cap && (rc = grow_arena(used + add, used))) break;
+            }
             int n_off = 0;
             kernel_ms = 0.f;
             for (int attempt = 0;; ++attempt) {
@@ -1075,13 +1091,15 @@ struct Builder {
             const size_t fin_smem = (size_t)kFinSmemKeys * 4;
             PSPC_TRY_CUDA(cudaFuncSetAttribute(k_finalize_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)fin_smem));
-            const int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
+            int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
+            if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
             k_finalize_merge<<<grid, kFinThreads, fin_smem, st>>>(F);
         } else {
             const size_t fin_smem = (size_t)kFinSmemKeys * 8;
             PSPC_TRY_CUDA(cudaFuncSetAttribute(k_finalize<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)fin_smem));
-            const int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
+            int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
+            if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
             k_finalize<false><<<grid, kFinThreads, fin_smem, st>>>(F);
         }
         out.launches += 1;
@@ -1137,7 +1155,7 @@ static void fill_defaults(pspc_opts& o, const pspc_opts* user) {
 }
 
 static bool opts_ok(const pspc_opts& o) {
-    return o.map_kind >= 0 && o.map_kind <= 3;
+    return o.map_kind >= 0 && o.map_kind <= 3 && o.max_ctas >= 0 && (o.granular == 0 || o.granular == 1);
 }
 
 static bool pow2_in(int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }

@@ -326,8 +326,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
     const int glane = tile.thread_rank();
     const uint64_t* seg_prev = A.seg + (int64_t)(d - 1) * n;
 
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(A.work, 1);
+    for (int round = 0;; ++round) {
+        if (tid == 0) s_item = A.granular ? (round == 0 ? (int)blockIdx.x : A.n_items) : atomicAdd(A.work, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= A.n_items) break;

@@ -57,6 +57,7 @@ struct LevelArgs {
     uint32_t cap_u_max;   // label hash slots (hash map kind)
     uint32_t bm_words;    // words per level bitmap (bitmap map kind)
     const int32_t* comp_base;  // first rank-space id of each vertex's graph in a batch (NULL: 0)
+    int granular;              // 1: CTA b handles item b only (grid = n_items); 0: persistent
     uint8_t* gscratch;    // per-CTA table memory when the tables are off chip
     size_t gscratch_stride;
 };

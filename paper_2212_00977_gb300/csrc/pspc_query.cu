@@ -293,6 +293,27 @@ __global__ void k_pair_scatter(const int32_t* __restrict__ pairs, int64_t q, int
     perm[atomicAdd(pos + ((s >= 0 && s < n) ? s : n), 1ull)] = (int32_t)p;
 }
 
+// All query kernels prefer the largest shared-memory carve-out, the
+// configuration the build kernels run in, so that query blocks can share
+// SMs with a build running on another stream instead of waiting for those
+// SMs to drain and change configuration.
+static void prefer_max_shared(const void* fn) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
+static std::once_flag g_carveout_once;
+
+static void set_query_carveouts() {
+    std::call_once(g_carveout_once, [] {
+        prefer_max_shared((const void*)k_query<8>);
+        prefer_max_shared((const void*)k_query<16>);
+        prefer_max_shared((const void*)k_query<32>);
+        prefer_max_shared((const void*)k_query_chunked<64>);
+        prefer_max_shared((const void*)k_query_chunked<128>);
+        prefer_max_shared((const void*)k_query_chunked<256>);
+    });
+}
+
 // Lanes per pair: wide groups for long labels (fewer merge steps), narrow
 // groups for short ones (more pairs in flight per warp).
 // Long labels: warp-staged chunks of 256 entries.
@@ -380,6 +401,7 @@ extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q,
         Q.out_cnt = dev_out ? count : d_cnt;
         Q.out_ovf = dev_out ? overflow : d_ovf;
         Q.err = d_err;
+        set_query_carveouts();
         const int G = query_group_for(ix);
         const void* fn = G == 8 ? (const void*)k_query<8>
                          : G == 16 ? (const void*)k_query<16>
@@ -560,6 +582,7 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
             Q.out_cnt = count;
             Q.out_ovf = overflow;
             Q.err = d_err;
+            set_query_carveouts();
             const int G = query_group_for(ix);
             const void* fn = G == 8 ? (const void*)k_query<8>
                              : G == 16 ? (const void*)k_query<16>
@@ -625,6 +648,7 @@ extern "C" int pspc_query_async(const pspc_index* hc, const int32_t* pairs, int6
     Q.out_cnt = count;
     Q.out_ovf = overflow;
     Q.err = err;
+    set_query_carveouts();
     const int G = query_group_for(ix);
     const void* fn = G == 8 ? (const void*)k_query<8>
                      : G == 16 ? (const void*)k_query<16>

@@ -78,8 +78,13 @@ class SPCServer:
         self.max_batch = int(max_batch_pairs)
         free, total = torch.cuda.mem_get_info(self.device)
         self.budget = int(memory_budget if memory_budget is not None else free * 0.8)
-        self.q_stream = torch.cuda.Stream(self.device)
-        self.b_stream = torch.cuda.Stream(self.device)
+        # Queries get the high-priority stream. Builds launch their level
+        # kernel one CTA per vertex (granular), so every finished vertex frees
+        # an SM slot that a pending query block takes first, and their off-chip
+        # pass keeps to one CTA per SM: a running build never holds the SMs
+        # for a whole level.
+        self.q_stream = torch.cuda.Stream(self.device, priority=-1)
+        self.b_stream = torch.cuda.Stream(self.device, priority=0)
         self.pairs_h = torch.empty((self.max_batch, 2), dtype=torch.int32, pin_memory=True)
         self.dist_h = torch.empty(self.max_batch, dtype=torch.uint16, pin_memory=True)
         self.cnt_h = torch.empty(self.max_batch, dtype=torch.uint64, pin_memory=True)
@@ -104,6 +109,9 @@ class SPCServer:
 
     # --- public API -------------------------------------------------------
     def add_index(self, name: str, ix: Index) -> None:
+        # The register-only query variant needs no shared memory, so its
+        # blocks fit on SMs whose shared memory a running build fills.
+        ix.set_query_group(32)
         st = ix.stats()
         with self.lock:
             self.indexes[name] = (ix, int(st["index_bytes"]))
@@ -233,7 +241,9 @@ class SPCServer:
                     continue
                 self.reserved += need
             try:
-                ix = Index.from_graph(g, rank, stream=self.b_stream, **r.opts)
+                opts = dict(r.opts)
+                opts.setdefault("granular", True)
+                ix = Index.from_graph(g, rank, stream=self.b_stream, **opts)
                 self.add_index(r.name, ix)
                 r.result = ix.stats()
             except Exception as e:  # surfaced to the caller through wait()

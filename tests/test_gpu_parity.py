@@ -170,7 +170,9 @@ def test_layout_invariance(pspc):
     outs = []
     for kw, dev in [(dict(), True), (dict(), False), (dict(cand_capacity=1024, label_capacity=1024), True),
                     (dict(cand_capacity=8192, label_capacity=16384), True), (dict(arena_entries=1), True),
-                    (dict(map_kind=2), True), (dict(map_kind=3), True), (dict(map_kind=2, label_capacity=1024), True)]:
+                    (dict(map_kind=2), True), (dict(map_kind=3), True), (dict(map_kind=2, label_capacity=1024), True),
+                    (dict(granular=True), True), (dict(max_ctas=8), True),
+                    (dict(granular=True, cand_capacity=1024, label_capacity=1024, map_kind=2), True)]:
         ix = gpu_index(pspc, g, rank, device=dev, **kw)
         assert_index_equal(ix, ref)
         outs.append(gpu_query(ix, pairs, device=dev))
