@@ -122,10 +122,17 @@ def level_kernel_traffic():
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = os.path.join(ROOT, "paper_2212_00977_gb300", "csrc", "pspc_build.cu")
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != d.get("source_sha256"):
+    if level_kernel_source_sha() != d.get("source_sha256"):
         return None
     return d.get("dram_bytes_per_launch")
+
+
+def level_kernel_source_sha() -> str:
+    """Hash of the level kernel's sources (the profile is stale once they change)."""
+    h = hashlib.sha256()
+    for f in ("pspc_level.cu", "pspc_level.cuh", "pspc_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2212_00977_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def level_algorithmic_bytes(ls):
