@@ -135,6 +135,23 @@ def level_kernel_source_sha() -> str:
     return h.hexdigest()
 
 
+def reduce_max(vals, dist, device):
+    """Max over ranks of each value (times: the slowest rank sets the pace)."""
+    if dist is None:
+        return list(vals)
+    import torch
+
+    t = torch.tensor(list(vals), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rates(entries, queries, steps, world, t_build_ms, t_query_ms):
+    """Whole-job throughput of N independent replicas: everything all ranks
+    built (queried) divided by the slowest rank's time."""
+    return (world * steps * entries / (t_build_ms / 1e3), world * steps * queries / (t_query_ms / 1e3))
+
+
 def level_algorithmic_bytes(ls):
     """Bytes any pull implementation must move at one level: the CSR arcs of
     the active vertices (4 B), every pulled entry (hub 4 B + count 8 B) and
@@ -251,13 +268,9 @@ def run_ours(args):
     T_build = sum(build_ms)
     T_query = sum(query_ms)
     T_step = T_build + T_query
-    if dist:
-        t = torch.tensor([T_build, T_query, T_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        T_build, T_query, T_step = t.tolist()
+    T_build, T_query, T_step = reduce_max([T_build, T_query, T_step], dist, dev)
     K = args.steps
-    value = world * K * entries / (T_build / 1e3)
-    qps = world * K * q / (T_query / 1e3)
+    value, qps = whole_job_rates(entries, q, K, world, T_build, T_query)
 
     # roofline of the level kernel (gather / merge / prune / append)
     kb = sum(level_algorithmic_bytes(l) for r in res for l in r[3])
