@@ -25,8 +25,12 @@
 //      L_<d(u) and L_<d(h) with d_u(x) + d_h(x) < d exists iff some
 //      x in L_k(h), 1 <= k <= d-2, has d_u(x) <= d-1-k (the case k = 0,
 //      x = h, was handled in step 2; entries of h at distance d-1 cannot
-//      help because d_u(x) >= 1 for x != u). Groups of 8 lanes scan these
-//      segments with early exit, taking candidates from a shared counter.
+//      help because d_u(x) >= 1 for x != u). Groups of lanes take
+//      candidates from a shared counter and scan these segments in level
+//      order with early exit: 8 lanes level by level when u has many
+//      candidates; 16 or 32 lanes over G levels' descriptors read at once,
+//      scanned as one list, when it has few (deep levels of high-diameter
+//      graphs), so that their lanes stay busy.
 //   4. Survivors are sorted by hub (bitonic, on chip) and appended to the
 //      label arena as L_d(u); the arena slot comes from one atomic add.
 #include <cooperative_groups.h>
@@ -38,7 +42,6 @@ namespace cg = cooperative_groups;
 
 namespace pspc {
 
-constexpr int kProbeGroup = 8;   // lanes per candidate in the prune scan
 constexpr int kProbeUnroll = 4;  // loads in flight per lane in the prune scan
 constexpr int kGatherUnroll = 4; // loads in flight per lane in the pull
 constexpr uint32_t kPrunedBit = 0x80000000u;
@@ -279,6 +282,118 @@ __device__ long long block_excl_scan_popc(const uint32_t* bits, uint32_t* wp, ui
     return total;
 }
 
+// Rule 2 for the candidates list[0..M): G lanes per candidate h. Lane j
+// reads the descriptor of level k0 + j of L(h) (levels 1..d-2, G at a time);
+// the lengths are prefix-summed over the group and the concatenated entries
+// scanned in level order, kProbeUnroll loads in flight per lane. The level of
+// entry i is the last lane whose exclusive prefix is <= i (a binary search
+// by shuffles). An entry x of level k is a witness iff d_u(x) <= d-1-k.
+template <int G, class Map>
+__device__ void prune_candidates(const Map& mp, const uint64_t* __restrict__ seg,
+                                 const uint32_t* __restrict__ hub_arena, int64_t n, int d, uint32_t* list,
+                                 const uint32_t* ckeys, int M, int* next) {
+    auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+    const int gl = tile.thread_rank();
+    for (;;) {
+        int c = 0;
+        if (gl == 0) c = atomicAdd(next, 1);
+        c = tile.shfl(c, 0);
+        if (c >= M) break;
+        const uint32_t slot = list[c];
+        const uint32_t h = ckeys[slot] & kHubMask;
+        bool pruned = false;
+        for (int k0 = 1; k0 <= d - 2 && !pruned; k0 += G) {
+            const int k = k0 + gl;
+            const uint64_t s = k <= d - 2 ? __ldg(seg + (int64_t)k * n + h) : 0ull;
+            const uint32_t len = seg_len(s);
+            const unsigned long long start = seg_start(s);
+            uint32_t incl = len;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const uint32_t t = tile.shfl_up(incl, o);
+                if (gl >= o) incl += t;
+            }
+            const uint32_t excl = incl - len;
+            const uint32_t total = tile.shfl(incl, G - 1);
+            for (uint32_t b = 0; b < total && !pruned; b += G * kProbeUnroll) {
+                uint32_t x[kProbeUnroll];
+                int thr[kProbeUnroll];
+#pragma unroll
+                for (int t = 0; t < kProbeUnroll; ++t) {
+                    const uint32_t i = b + t * G + gl;
+                    int j = 0;
+#pragma unroll
+                    for (int step = G >> 1; step > 0; step >>= 1) {
+                        const uint32_t e = tile.shfl(excl, j + step);
+                        if (e <= i) j += step;
+                    }
+                    const unsigned long long sj = tile.shfl(start, j);
+                    const uint32_t ej = tile.shfl(excl, j);
+                    thr[t] = d - 1 - (k0 + j);
+                    x[t] = i < total ? (__ldg(hub_arena + sj + (i - ej)) & kHubMask) : kEmpty;
+                }
+                bool hit = false;
+#pragma unroll
+                for (int t = 0; t < kProbeUnroll; ++t)
+                    if (x[t] != kEmpty) hit |= mp.within(x[t], thr[t]);
+                pruned = tile.any(hit);
+            }
+        }
+        if (pruned && gl == 0) list[c] = slot | kPrunedBit;
+    }
+}
+
+// Rule 2 level by level: G lanes per candidate scan L_1(h), then L_2(h), ...
+// (one descriptor read per level), kProbeUnroll loads in flight per lane.
+template <int G, class Map>
+__device__ void prune_by_level(const Map& mp, const uint64_t* __restrict__ seg,
+                               const uint32_t* __restrict__ hub_arena, int64_t n, int d, uint32_t* list,
+                               const uint32_t* ckeys, int M, int* next) {
+    auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+    const int gl = tile.thread_rank();
+    for (;;) {
+        int c = 0;
+        if (gl == 0) c = atomicAdd(next, 1);
+        c = tile.shfl(c, 0);
+        if (c >= M) break;
+        const uint32_t slot = list[c];
+        const uint32_t h = ckeys[slot] & kHubMask;
+        bool pruned = false;
+        for (int k = 1; k <= d - 2 && !pruned; ++k) {
+            const uint64_t s = __ldg(seg + (int64_t)k * n + h);
+            const uint32_t len = seg_len(s);
+            const uint32_t* xs = hub_arena + seg_start(s);
+            const int thr = d - 1 - k;
+            for (uint32_t b = 0; b < len && !pruned; b += G * kProbeUnroll) {
+                uint32_t x[kProbeUnroll];
+#pragma unroll
+                for (int t = 0; t < kProbeUnroll; ++t) {
+                    const uint32_t i = b + t * G + gl;
+                    x[t] = i < len ? (__ldg(xs + i) & kHubMask) : kEmpty;
+                }
+                bool hit = false;
+#pragma unroll
+                for (int t = 0; t < kProbeUnroll; ++t)
+                    if (x[t] != kEmpty) hit |= mp.within(x[t], thr);
+                pruned = tile.any(hit);
+            }
+        }
+        if (pruned && gl == 0) list[c] = slot | kPrunedBit;
+    }
+}
+
+// Many candidates: 8 lanes each, level by level (most are pruned within the
+// first entries of L_1(h), so reading further descriptors up front only
+// costs loads). Few candidates: wider groups over the concatenated levels,
+// so that the long scans of deep levels keep all lanes busy.
+template <class Map>
+__device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, const uint32_t* hub_arena, int64_t n,
+                                          int d, uint32_t* list, const uint32_t* ckeys, int M, int* next) {
+    if (M >= 64) prune_by_level<8>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
+    else if (M >= 16) prune_candidates<16>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
+    else prune_candidates<32>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
+}
+
 __device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
     for (uint32_t k = 2; k <= P; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -322,8 +437,6 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kLevelThreads / 32;
-    auto tile = cg::tiled_partition<kProbeGroup>(cg::this_thread_block());
-    const int glane = tile.thread_rank();
     const uint64_t* seg_prev = A.seg + (int64_t)(d - 1) * n;
 
     for (int round = 0;; ++round) {
@@ -534,39 +647,10 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         }
 
         // 3. prune rule 2 over levels 1..d-2 of each candidate's label
-        if (d >= 3 && !marked) {
-            for (;;) {
-                int c = 0;
-                if (glane == 0) c = atomicAdd(&s_next, 1);
-                c = tile.shfl(c, 0);
-                if (c >= M) break;
-                const uint32_t slot = list[c];
-                const uint32_t h = ckeys[slot] & kHubMask;
-                bool pruned = false;
-                for (int k = 1; k <= d - 2 && !pruned; ++k) {
-                    const uint64_t s = __ldg(A.seg + (int64_t)k * n + h);
-                    const uint32_t len = seg_len(s);
-                    const uint32_t* xs = A.hub_arena + seg_start(s);
-                    const int thr = d - 1 - k;
-                    for (uint32_t b = 0; b < len && !pruned; b += kProbeGroup * kProbeUnroll) {
-                        uint32_t x[kProbeUnroll];
-#pragma unroll
-                        for (int t = 0; t < kProbeUnroll; ++t) {
-                            const uint32_t i = b + t * kProbeGroup + glane;
-                            x[t] = i < len ? (__ldg(xs + i) & kHubMask) : kEmpty;
-                        }
-                        bool hit = false;
-#pragma unroll
-                        for (int t = 0; t < kProbeUnroll; ++t)
-                            if (x[t] != kEmpty)
-                                hit |= kMap == kMapBitmap ? bm.within(x[t], thr)
-                                       : kMap == kMapHash ? hm.within(x[t], thr)
-                                                          : sm.within(x[t], thr);
-                        pruned = tile.any(hit);
-                    }
-                }
-                if (pruned && glane == 0) list[c] = slot | kPrunedBit;
-            }
+        if (d >= 3 && !marked && M > 0) {
+            if constexpr (kMap == kMapBitmap) prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M, &s_next);
+            else if constexpr (kMap == kMapHash) prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M, &s_next);
+            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M, &s_next);
             __syncthreads();
         }
 
