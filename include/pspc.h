@@ -88,6 +88,15 @@ typedef struct {
                                 work on a higher-priority stream (a query
                                 batch next to a build) gets SMs as soon as
                                 any vertex finishes; same results */
+    int32_t landmarks;       /* landmark filter of pruning rule 2 (Section
+                                "Landmark-Based Filtering"): the K highest-
+                                ranked vertices of every graph are
+                                landmarks, and their exact BFS distances to
+                                every vertex (one byte each) let the prune
+                                step drop a candidate h of u at level d at
+                                once when sd(u,l) + sd(l,h) < d for some
+                                landmark l. 0 = default (K = 32), -1 = off,
+                                1..64 = K. Results do not depend on it */
 } pspc_opts;
 
 /* Per-level counters of the last build (level d = distance d). */
@@ -100,6 +109,8 @@ typedef struct {
     float ms;                  /* device time of the whole level */
     float kernel_ms;           /* device time of the level's gather/merge/
                                   prune/append kernel launches only */
+    int64_t landmark_pruned;   /* candidates the landmark filter dropped
+                                  (the rest went through the label scan) */
 } pspc_level_stat_t;
 
 typedef struct {
@@ -115,6 +126,8 @@ typedef struct {
                                       calls on this index so far */
     int32_t graphs;      /* graphs the index was built from (1, or k of a batch) */
     float build_ms;      /* device time of pspc_build, input checks included */
+    int32_t landmarks;   /* landmarks per graph used by the build (0: none) */
+    float landmark_ms;   /* device time of the landmark BFS within build_ms */
 } pspc_stats_t;
 
 /* One graph of a batch: symmetric CSR as in pspc_csr, plus its order. */
@@ -275,6 +288,19 @@ int pspc_set_query_group(pspc_index* ix, int32_t lanes);
 #define PSPC_NOALLOC_SCRATCH_BYTES (16u << 20)
 int pspc_query_noalloc(const pspc_index* ix, const int32_t* pairs, int64_t q, uint16_t* dist,
                        uint64_t* count, uint8_t* overflow, void* stream);
+
+/*
+ * pspc_landmarks -- the landmark distances the build used for its landmark
+ * filter (Section "Landmark-Based Filtering"; the landmarks of a graph are
+ * its k highest-ranked vertices, k = pspc_opts.landmarks).
+ * k:    host int32 out; the landmarks per graph (0 when the filter was off).
+ * dist: NULL, or host uint8[n][k] out by caller vertex id: dist[v*k + j] =
+ *       sd(v, j-th highest-ranked vertex of v's graph), or 255 when that
+ *       distance is above 254, the two are not connected, or v's graph has
+ *       no j-th vertex.
+ * Errors: PSPC_E_INVAL (NULL index or k), PSPC_E_NOMEM, PSPC_E_CUDA.
+ */
+int pspc_landmarks(const pspc_index* ix, int32_t* k, uint8_t* dist);
 
 /* pspc_free -- release an index and all its device memory; NULL is a no-op. */
 void pspc_free(pspc_index* ix);

@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("cand_capacity", ctypes.c_int32), ("label_capacity", ctypes.c_int32),
                 ("arena_entries", ctypes.c_int64), ("max_levels", ctypes.c_int32),
                 ("verbose", ctypes.c_int32), ("map_kind", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-                ("granular", ctypes.c_int32)]
+                ("granular", ctypes.c_int32), ("landmarks", ctypes.c_int32)]
 
 
 class GraphDesc(ctypes.Structure):
@@ -58,7 +58,8 @@ class GraphDesc(ctypes.Structure):
 class LevelStat(ctypes.Structure):
     _fields_ = [("raw_candidates", ctypes.c_int64), ("unique_candidates", ctypes.c_int64),
                 ("entries", ctypes.c_int64), ("active_vertices", ctypes.c_int64),
-                ("active_arcs", ctypes.c_int64), ("ms", ctypes.c_float), ("kernel_ms", ctypes.c_float)]
+                ("active_arcs", ctypes.c_int64), ("ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                ("landmark_pruned", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -66,7 +67,8 @@ class Stats(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("index_bytes", ctypes.c_int64), ("overflow_entries", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("query_kernel_launches", ctypes.c_int64),
-                ("graphs", ctypes.c_int32), ("build_ms", ctypes.c_float)]
+                ("graphs", ctypes.c_int32), ("build_ms", ctypes.c_float),
+                ("landmarks", ctypes.c_int32), ("landmark_ms", ctypes.c_float)]
 
 
 # Every symbol include/pspc.h declares, with its ctypes signature.
@@ -85,6 +87,7 @@ _SIGS = {
     "pspc_export_vertices": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     "pspc_hub_column": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "pspc_query_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
+    "pspc_landmarks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), _P]),
     "pspc_free": (None, [_P]),
     "pspc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -160,7 +163,7 @@ class Index:
     @classmethod
     def build(cls, n: int, row_ptr, col, rank, *, stream=None, cand_capacity=0, label_capacity=0,
               arena_entries=0, max_levels=0, verbose=False, map_kind=0, max_ctas=0,
-              granular=False) -> "Index":
+              granular=False, landmarks=0) -> "Index":
         """pspc_build over a symmetric CSR (rows strictly ascending) and a
         rank permutation (0 = highest)."""
         lib = load()
@@ -169,7 +172,7 @@ class Index:
         _check_dtype(rank, np.int32, "rank")
         g = Csr(int(n), _ptr(row_ptr), _ptr(col))
         o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
-                 int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)))
+                 int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)), int(landmarks))
         h = _P()
         rc = lib.pspc_build(ctypes.byref(g), _ptr(rank), ctypes.byref(o), ctypes.byref(h),
                             _stream_handle(stream))
@@ -180,7 +183,7 @@ class Index:
     @classmethod
     def build_batch(cls, graphs, *, stream=None, cand_capacity=0, label_capacity=0, arena_entries=0,
                     max_levels=0, verbose=False, map_kind=0, max_ctas=0,
-              granular=False) -> "Index":
+                    granular=False, landmarks=0) -> "Index":
         """pspc_build_batch over ``graphs`` = [(n, row_ptr, col, rank), ...]:
         one index over their disjoint union (graph g's vertex v has id
         base_g + v, base_g = sum of earlier n)."""
@@ -195,7 +198,7 @@ class Index:
             keep.append((rp, col, rank))
             arr[i] = GraphDesc(int(n), _ptr(rp), _ptr(col), _ptr(rank))
         o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
-                 int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)))
+                 int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)), int(landmarks))
         h = _P()
         rc = lib.pspc_build_batch(ctypes.cast(arr, ctypes.c_void_p), k, ctypes.byref(o), ctypes.byref(h),
                                   _stream_handle(stream))
@@ -254,6 +257,22 @@ class Index:
         if rc != PSPC_OK:
             raise PSPCError(rc, "pspc_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def landmarks(self) -> np.ndarray:
+        """pspc_landmarks: uint8 [n, k] distances from each vertex to the k
+        highest-ranked vertices of its graph (255 = above 254 or none);
+        k = 0 when the build ran without the landmark filter."""
+        lib = load()
+        k = ctypes.c_int32()
+        rc = lib.pspc_landmarks(self._h, ctypes.byref(k), None)
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_landmarks")
+        out = np.empty((self.n, k.value), dtype=np.uint8)
+        if k.value:
+            rc = lib.pspc_landmarks(self._h, ctypes.byref(k), _ptr(out))
+            if rc != PSPC_OK:
+                raise PSPCError(rc, "pspc_landmarks")
+        return out
 
     def level_stats(self) -> list[dict]:
         lib = load()

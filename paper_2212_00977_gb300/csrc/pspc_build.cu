@@ -531,6 +531,7 @@ struct Builder {
         dfree(out.hub, st);
         dfree(out.dist, st);
         dfree(out.cnt, st);
+        dfree(out.lmk, st);
         cudaStreamSynchronize(st);
     }
 
@@ -830,6 +831,8 @@ struct Builder {
         A.stt = stt;
         A.retry_list = glist + hstt->n_global;
         A.comp_base = comp_base;
+        A.lmk = out.lmk;
+        A.lmk_stride = out.lmk_stride;
         if (hstt->n_smem > 0) {
             A.items = items;
             A.n_items = hstt->n_smem;
@@ -920,6 +923,28 @@ struct Builder {
         return PSPC_OK;
     }
 
+    // Landmark labelling (Section "Landmark-Based Filtering"): distances
+    // from the o.landmarks highest-ranked vertices of every graph, kept with
+    // the index.
+    int landmarks() {
+        out.lmk_k = o.landmarks;
+        out.lmk_stride = (o.landmarks + 15) / 16 * 16;
+        PSPC_TRY_CUDA(dalloc(&out.lmk, n * out.lmk_stride, st));
+        cudaEvent_t a, b;
+        PSPC_TRY_CUDA(cudaEventCreate(&a));
+        PSPC_TRY_CUDA(cudaEventCreate(&b));
+        cudaEventRecord(a, st);
+        int rc = landmark_bfs(n, rp_r, col_r, comp_base, out.lmk_k, out.lmk_stride, out.lmk, st, &out.launches);
+        cudaEventRecord(b, st);
+        if (!rc) {
+            cudaEventSynchronize(b);
+            cudaEventElapsedTime(&out.lmk_ms, a, b);
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return rc;
+    }
+
     int build_levels() {
         PSPC_TRY_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         LevelPlan plan;
@@ -943,6 +968,7 @@ struct Builder {
         k_level0<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, hub_arena, cnt_arena, seg);
         out.launches += 1;
         PSPC_TRY_CUDA(cudaGetLastError());
+        if (o.landmarks > 0 && (rc = landmarks())) return rc;
         lvl_base.assign({0ull, (unsigned long long)n});
         unsigned long long bump = (unsigned long long)n;
         cudaEvent_t e0, e1;
@@ -960,7 +986,7 @@ struct Builder {
             if ((rc = plan_level(d, plan))) break;
             cudaEventRecord(e0, st);
             if (d == 1) {
-                pspc_level_stat_t ls;
+                pspc_level_stat_t ls{};
                 cudaMemsetAsync(seg + n, 0, n * 8, st);
                 if ((rc = level1(bump, ls))) break;
                 cudaEventRecord(e1, st);
@@ -1011,6 +1037,7 @@ struct Builder {
                 LevelStatus keep = *hstt;
                 keep.bump = lvl_base[d];
                 keep.unique_total = 0;
+                keep.lmk_pruned = 0;
                 keep.n_retry = 0;
                 keep.arena_overflow = 0;
                 keep.work_smem = keep.work_global = 0;
@@ -1024,7 +1051,7 @@ struct Builder {
             float ms = 0.f;
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&ms, e0, e1);
-            pspc_level_stat_t ls;
+            pspc_level_stat_t ls{};
             ls.raw_candidates = raw_total;
             ls.unique_candidates = (long long)hstt->unique_total;
             ls.entries = added;
@@ -1032,6 +1059,7 @@ struct Builder {
             ls.active_arcs = active_arcs;
             ls.ms = ms;
             ls.kernel_ms = kernel_ms;
+            ls.landmark_pruned = (long long)hstt->lmk_pruned;
             out.lstats.push_back(ls);
             if (o.verbose)
                 fprintf(stderr, "pspc level %d: raw %lld unique %lld entries %lld active %d (off-chip %d) %.3f ms\n",
@@ -1152,10 +1180,12 @@ static void fill_defaults(pspc_opts& o, const pspc_opts* user) {
     if (o.cand_capacity <= 0) o.cand_capacity = 4096;
     if (o.label_capacity <= 0) o.label_capacity = 8192;
     if (o.max_levels <= 0) o.max_levels = kMaxDist;
+    if (o.landmarks == 0) o.landmarks = 32;
 }
 
 static bool opts_ok(const pspc_opts& o) {
-    return o.map_kind >= 0 && o.map_kind <= 3 && o.max_ctas >= 0 && (o.granular == 0 || o.granular == 1);
+    return o.map_kind >= 0 && o.map_kind <= 3 && o.max_ctas >= 0 && (o.granular == 0 || o.granular == 1) &&
+           o.landmarks >= -1 && o.landmarks <= 64;
 }
 
 static bool pow2_in(int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
@@ -1207,6 +1237,7 @@ static int run_build(const pspc_opts* opts, pspc_index** out, void* stream, int3
     B.out.hub = nullptr;
     B.out.dist = nullptr;
     B.out.cnt = nullptr;
+    B.out.lmk = nullptr;
     *out = h;
     return PSPC_OK;
 }

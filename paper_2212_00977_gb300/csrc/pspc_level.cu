@@ -21,7 +21,10 @@
 //      so rule 2 would prune it (Label Elimination at no cost). The others
 //      are merged per hub in an on-chip hash (count += c mod 2^64; the
 //      overflow flag takes the entry's flag and the carry: Label Merging).
-//   3. Prune (rule 2) for every merged candidate h. A common hub x of
+//   3. Landmark filter (Section "Landmark-Based Filtering"), when the build
+//      has landmark distances: a candidate h with sd(u,l) + sd(l,h) < d for
+//      a landmark l is pruned at once; the others are compacted and go on.
+//      Prune (rule 2) for every remaining candidate h. A common hub x of
 //      L_<d(u) and L_<d(h) with d_u(x) + d_h(x) < d exists iff some
 //      x in L_k(h), 1 <= k <= d-2, has d_u(x) <= d-1-k (the case k = 0,
 //      x = h, was handled in step 2; entries of h at distance d-1 cannot
@@ -394,6 +397,55 @@ __device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, co
     else prune_candidates<32>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
 }
 
+// Landmark filter (Section "Landmark-Based Filtering"): candidate h of u at
+// level d is pruned at once when some landmark l has sd(u,l) + sd(l,h) < d,
+// for then sd(u,h) < d, which is exactly when rule 2's query over the labels
+// below d prunes it. Distances are bytes (255 = unknown), added with
+// saturation and compared with min(d, 255), so an unknown or saturated sum
+// never prunes. The candidates left are compacted to list[0..kept) in the
+// same order (in rounds of one candidate per thread: every read of a round
+// precedes its writes, and no write reaches past the round's reads).
+__device__ int landmark_filter(const LevelArgs& A, const uint32_t* s_lmk, int d, uint32_t* list,
+                               const uint32_t* ckeys, int M, int* s_wcnt, int* s_kept) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t dd = (uint32_t)(d < 255 ? d : 255) * 0x01010101u;
+    const int words = A.lmk_stride / 16;
+    int kept = 0;
+    for (int base = 0; base < M; base += kLevelThreads) {
+        const int c = base + tid;
+        uint32_t slot = 0;
+        bool keep = false;
+        if (c < M) {
+            slot = list[c];
+            const uint4* row = (const uint4*)(A.lmk + (size_t)(ckeys[slot] & kHubMask) * A.lmk_stride);
+            uint32_t hit = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                if (w < words) {
+                    const uint4 b = __ldg(row + w);
+                    hit |= __vcmpltu4(__vaddus4(s_lmk[4 * w + 0], b.x), dd) |
+                           __vcmpltu4(__vaddus4(s_lmk[4 * w + 1], b.y), dd) |
+                           __vcmpltu4(__vaddus4(s_lmk[4 * w + 2], b.z), dd) |
+                           __vcmpltu4(__vaddus4(s_lmk[4 * w + 3], b.w), dd);
+                }
+            keep = hit == 0u;
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, round = 0;
+        for (int w = 0; w < kLevelThreads / 32; ++w) {
+            before += w < warp ? s_wcnt[w] : 0;
+            round += s_wcnt[w];
+        }
+        if (keep) list[kept + before + __popc(bal & ((1u << lane) - 1u))] = slot;
+        kept += round;
+        __syncthreads();
+    }
+    if (tid == 0) *s_kept = kept;
+    return kept;
+}
+
 __device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
     for (uint32_t k = 2; k <= P; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -418,7 +470,9 @@ __device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
 template <int kMap, bool kOffChip>
 __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_item, s_nkeys, s_abort, s_m, s_next, s_nsurv;
+    __shared__ int s_item, s_nkeys, s_abort, s_m, s_next, s_nsurv, s_kept;
+    __shared__ uint32_t s_lmk[16];  // u's landmark distances (bytes)
+    __shared__ int s_wcnt[kLevelThreads / 32];
     __shared__ unsigned long long s_base;
     __shared__ long long s_wsum[kLevelThreads / 32];
 
@@ -485,6 +539,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             s_next = 0;
             s_nsurv = 0;
         }
+        if (A.lmk && tid < A.lmk_stride / 4) s_lmk[tid] = __ldg((const uint32_t*)(A.lmk + u * A.lmk_stride) + tid);
         __syncthreads();
 
         // 1. label map of L_<d(u)
@@ -566,7 +621,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         for (uint32_t slot = tid; slot < cap_c; slot += kLevelThreads)
             if (ckeys[slot] != kEmpty) list[atomicAdd(&s_m, 1)] = slot;
         __syncthreads();
-        const int M = s_m;
+        int M = s_m;
 
         // 3a. d = 3: rule 2 asks for a common neighbour x of u and h ranked
         // above h (x in L_1(u) and x in L_1(h)). Walk, for every x in L_1(u),
@@ -647,12 +702,18 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         }
 
         // 3. prune rule 2 over levels 1..d-2 of each candidate's label
-        if (d >= 3 && !marked && M > 0) {
-            if constexpr (kMap == kMapBitmap) prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M, &s_next);
-            else if constexpr (kMap == kMapHash) prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M, &s_next);
-            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M, &s_next);
+        int M_scan = M;
+        if (d >= 3 && !marked && M > 0 && A.lmk) {
+            M_scan = landmark_filter(A, s_lmk, d, list, ckeys, M, s_wcnt, &s_kept);
+            if (tid == 0 && M_scan < M) atomicAdd(&A.stt->lmk_pruned, (unsigned long long)(M - M_scan));
+        }
+        if (d >= 3 && !marked && M_scan > 0) {
+            if constexpr (kMap == kMapBitmap) prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, &s_next);
+            else if constexpr (kMap == kMapHash) prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, &s_next);
+            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, &s_next);
             __syncthreads();
         }
+        M = M_scan;  // list[0..M) now holds every candidate that can survive
 
         // 4. survivors, hub-sorted, appended as L_d(u). Candidate hubs are < u:
         // when a bitmap of u bits and its word prefix fit the map region, a

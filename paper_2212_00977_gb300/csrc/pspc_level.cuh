@@ -26,6 +26,7 @@ struct LevelStatus {
     int n_smem;
     int n_global;
     int n_retry;
+    unsigned long long lmk_pruned;  // candidates dropped by the landmark filter
     int arena_overflow;
     int work_smem;
     int work_global;
@@ -60,6 +61,8 @@ struct LevelArgs {
     int granular;              // 1: CTA b handles item b only (grid = n_items); 0: persistent
     uint8_t* gscratch;    // per-CTA table memory when the tables are off chip
     size_t gscratch_stride;
+    const uint8_t* lmk;   // [n][lmk_stride] landmark distances, or NULL (no filter)
+    int lmk_stride;       // multiple of 16, <= 64
 };
 
 // Table layout (on chip, or in per-CTA device scratch). The map region also
@@ -109,6 +112,14 @@ enum MapKind { kMapBitmap = 0, kMapHash = 1, kMapSeg = 2 };
 __host__ __device__ inline size_t level_map_bytes(int kind, int d, uint32_t bm_words, uint32_t cap_u) {
     return kind == kMapBitmap ? bitmap_bytes(d, bm_words) : kind == kMapHash ? hashmap_bytes(cap_u) : 0;
 }
+
+// Landmark labelling (pspc_landmark.cu): exact BFS distances from the k
+// highest-ranked vertices of every graph (rank-space ids comp_base[v] + j,
+// or j when comp_base is NULL), all k searches at once with one 64-bit mask
+// of reached landmarks per vertex. ld is [n][stride] bytes, 255 where the
+// distance is above 254 or undefined. Synchronises st once per BFS level.
+int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* comp_base, int k, int stride,
+                 uint8_t* ld, cudaStream_t st, int64_t* launches);
 
 // Launchers (pspc_level.cu). Each returns a CUDA error code of the launch.
 cudaError_t launch_arc_src(const int64_t* rp, int64_t n, int32_t* arc_src, cudaStream_t st);

@@ -174,6 +174,7 @@ extern "C" void pspc_free(pspc_index* h) {
     dev_free(ix.hub, 0);
     dev_free(ix.dist, 0);
     dev_free(ix.cnt, 0);
+    dev_free(ix.lmk, 0);
     cudaStreamSynchronize(0);
     cudaSetDevice(prev);
     delete h;
@@ -194,7 +195,37 @@ extern "C" int pspc_stats(const pspc_index* h, pspc_stats_t* s) {
     s->query_kernel_launches = ix.query_launches;
     s->graphs = ix.graphs;
     s->build_ms = ix.build_ms;
+    s->landmarks = ix.lmk ? ix.lmk_k : 0;
+    s->landmark_ms = ix.lmk_ms;
     return PSPC_OK;
+}
+
+extern "C" int pspc_landmarks(const pspc_index* h, int32_t* k, uint8_t* dist) {
+    if (!h || !k) return PSPC_E_INVAL;
+    const Index& ix = h->ix;
+    *k = ix.lmk ? ix.lmk_k : 0;
+    if (!dist || !ix.lmk) return PSPC_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ix.device);
+    const size_t S = (size_t)ix.lmk_stride, K = (size_t)ix.lmk_k;
+    std::vector<uint8_t> rows;
+    std::vector<int32_t> rank;
+    int rc = PSPC_OK;
+    try {
+        rows.resize((size_t)ix.n * S);
+        rank.resize((size_t)ix.n);
+    } catch (...) {
+        rc = PSPC_E_NOMEM;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = cudaMemcpy(rows.data(), ix.lmk, rows.size(), cudaMemcpyDeviceToHost);
+    if (!rc && e == cudaSuccess) e = cudaMemcpy(rank.data(), ix.rank, (size_t)ix.n * 4, cudaMemcpyDeviceToHost);
+    if (!rc && e != cudaSuccess) rc = cuda_status(e);
+    if (!rc)
+        for (int64_t v = 0; v < ix.n; ++v) memcpy(dist + (size_t)v * K, rows.data() + (size_t)rank[v] * S, K);
+    cudaSetDevice(prev);
+    return rc;
 }
 
 extern "C" int pspc_level_stats(const pspc_index* h, pspc_level_stat_t* out, int32_t cap,

@@ -72,7 +72,7 @@ def test_paper_table(pspc):
 # --- small graphs against the oracle, across table capacities ---
 
 CAPS = [dict(), dict(cand_capacity=1024, label_capacity=1024), dict(map_kind=2, label_capacity=1024),
-        dict(map_kind=3)]
+        dict(map_kind=3), dict(landmarks=-1), dict(landmarks=64, map_kind=3)]
 
 
 @pytest.mark.parametrize("seed", range(10))
