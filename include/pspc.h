@@ -257,9 +257,15 @@ int pspc_level_stats(const pspc_index* ix, pspc_level_stat_t* out, int32_t cap,
  * pspc_set_query_group -- tuning hook for pspc_query: how one pair is
  * merge-joined. 8, 16 or 32 = that many lanes compare 32-bit hub words held
  * in registers; 64, 128 or 256 = one warp stages chunks of that many
- * entries of both labels in shared memory; 0 = chosen from the average
- * label size. Results do not depend on it. Errors: PSPC_E_INVAL.
+ * entries of both labels in shared memory; PSPC_QUERY_BY_SOURCE = pairs
+ * sorted by source, L(s) held in an on-chip hash for every pair of that
+ * source and each pair streams only L(t) (used when the call groups its
+ * pairs by source, q >= 4096 and q >= n/4, and the largest label has at
+ * most 8192 entries; otherwise 0 applies); 0 = PSPC_QUERY_BY_SOURCE when
+ * it applies and q >= 64 n, else chosen from the average label size.
+ * Results do not depend on it. Errors: PSPC_E_INVAL.
  */
+#define PSPC_QUERY_BY_SOURCE 1
 int pspc_set_query_group(pspc_index* ix, int32_t lanes);
 
 /*

@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import math
 
-QUERY_VARIANTS = (16, 32, 64, 128, 256)
+QUERY_VARIANTS = (1, 16, 32, 64, 128, 256)  # 1 = by source (pspc.PSPC_QUERY_BY_SOURCE)
 BUILD_VARIANTS = tuple(dict(cand_capacity=c, map_kind=m) for c in (2048, 4096, 8192) for m in (0, 2, 3))
 
 _cache: dict = {}

@@ -287,14 +287,24 @@ __device__ void fin_bitonic_sort(unsigned long long* buf, uint32_t P) {
 // ---------------------------------------------------------------------------
 // Finalize: merge each vertex's level segments into one hub-sorted label.
 
+// Label sizes (into off, scanned later), the vertices whose labels need the
+// off-chip finalize, and the largest label size (max_lab, by warp maxima).
 __global__ void k_fin_sizes(int64_t n, int levels, const uint64_t* __restrict__ seg, int64_t* __restrict__ off,
-                            int32_t* __restrict__ big, int* n_big) {
+                            int32_t* __restrict__ big, int* n_big, unsigned long long* max_lab) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= n) return;
     int64_t t = 0;
-    for (int l = 0; l < levels; ++l) t += seg_len(seg[(int64_t)l * n + u]);
-    off[u] = t;
-    if (t > kFinSmemKeys) big[atomicAdd(n_big, 1)] = (int32_t)u;
+    if (u < n) {
+        for (int l = 0; l < levels; ++l) t += seg_len(seg[(int64_t)l * n + u]);
+        off[u] = t;
+        if (t > kFinSmemKeys) big[atomicAdd(n_big, 1)] = (int32_t)u;
+    }
+    unsigned long long m = (unsigned long long)t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+        m = x > m ? x : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(max_lab, m);
 }
 
 struct FinArgs {
@@ -1085,11 +1095,11 @@ struct Builder {
         PSPC_TRY_CUDA(dalloc(&big, n, st));
         PSPC_TRY_CUDA(dalloc(&ctr, 2, st));
         PSPC_TRY_CUDA(dalloc(&d_lvl, lvl_base.size(), st));
-        PSPC_TRY_CUDA(dalloc(&n_ovf, 1, st));
+        PSPC_TRY_CUDA(dalloc(&n_ovf, 2, st));  // [0] overflow entries, [1] largest label
         PSPC_TRY_CUDA(cudaMemsetAsync(ctr, 0, 8, st));
-        PSPC_TRY_CUDA(cudaMemsetAsync(n_ovf, 0, 8, st));
+        PSPC_TRY_CUDA(cudaMemsetAsync(n_ovf, 0, 16, st));
         PSPC_TRY_CUDA(cudaMemcpyAsync(d_lvl, lvl_base.data(), lvl_base.size() * 8, cudaMemcpyHostToDevice, st));
-        k_fin_sizes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, L, seg, out.off, big, ctr);
+        k_fin_sizes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, L, seg, out.off, big, ctr, n_ovf + 1);
         out.launches += 1;
         PSPC_TRY_CUDA(cudaGetLastError());
         int rc = exclusive_scan_i64(out.off, n, st, &out.launches);
@@ -1097,7 +1107,10 @@ struct Builder {
         int hbig[2] = {0, 0};
         PSPC_TRY_CUDA(cudaMemcpyAsync(&out.entries, out.off + n, 8, cudaMemcpyDeviceToHost, st));
         PSPC_TRY_CUDA(cudaMemcpyAsync(hbig, ctr, 8, cudaMemcpyDeviceToHost, st));
+        unsigned long long hmax = 0;
+        PSPC_TRY_CUDA(cudaMemcpyAsync(&hmax, n_ovf + 1, 8, cudaMemcpyDeviceToHost, st));
         PSPC_TRY_CUDA(cudaStreamSynchronize(st));
+        out.max_label = (int64_t)hmax;
         const int64_t E = out.entries;
         PSPC_TRY_CUDA(dalloc(&out.hub, E, st));
         PSPC_TRY_CUDA(dalloc(&out.dist, E, st));

@@ -48,6 +48,7 @@ struct Index {
     uint16_t* dist = nullptr;  // distance | overflow << 15
     uint64_t* cnt = nullptr;   // trough path count mod 2^64
     int64_t entries = 0;
+    int64_t max_label = 0;     // entries of the largest label
     int32_t levels = 0;
     int64_t overflow_entries = 0;
     float build_ms = 0.f;

@@ -52,6 +52,43 @@ __device__ __forceinline__ void add_term(uint64_t& sum, uint32_t& flag, uint64_t
     sum = s;
 }
 
+// Warp-wide end of one pair: the minimum distance over the lanes, the sum
+// (mod 2^64, sticky flag) of the lanes' partial sums at that minimum, and
+// lane 0 writes the answer of pair p.
+__device__ __forceinline__ void finish_pair_warp(const QueryArgs& Q, int64_t p, uint32_t best, uint64_t sum,
+                                                 uint32_t flag, int lane) {
+    uint32_t gbest = best;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gbest = min(gbest, __shfl_xor_sync(0xFFFFFFFFu, gbest, o));
+    if (best != gbest) {
+        sum = 0;
+        flag = 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t os = __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        const uint32_t of = __shfl_xor_sync(0xFFFFFFFFu, flag, o);
+        add_term(sum, flag, os, of);
+    }
+    if (lane == 0) {
+        if (gbest == 0xFFFFFFFFu) {
+            Q.out_dist[p] = PSPC_UNREACHED;
+            Q.out_cnt[p] = 0;
+            if (Q.out_ovf) Q.out_ovf[p] = 0;
+        } else {
+            Q.out_dist[p] = (uint16_t)gbest;
+            Q.out_cnt[p] = sum;
+            if (Q.out_ovf) Q.out_ovf[p] = (uint8_t)(flag != 0);
+        }
+    }
+}
+
+__device__ __forceinline__ void write_fixed(const QueryArgs& Q, int64_t p, uint16_t d, uint64_t c) {
+    Q.out_dist[p] = d;
+    Q.out_cnt[p] = c;
+    if (Q.out_ovf) Q.out_ovf[p] = 0;
+}
+
 template <int G>
 __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs Q) {
     auto tile = cg::tiled_partition<G>(cg::this_thread_block());
@@ -247,30 +284,129 @@ __global__ void __launch_bounds__(kQueryThreads) k_query_chunked(const QueryArgs
             if (load_a) ia += na;
             if (load_b) ib += nb;
         }
-        uint32_t gbest = best;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gbest = min(gbest, __shfl_xor_sync(0xFFFFFFFFu, gbest, o));
-        if (best != gbest) {
-            sum = 0;
-            flag = 0;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t os = __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-            const uint32_t of = __shfl_xor_sync(0xFFFFFFFFu, flag, o);
-            add_term(sum, flag, os, of);
-        }
-        if (lane == 0) {
-            if (gbest == 0xFFFFFFFFu) {
-                Q.out_dist[p] = PSPC_UNREACHED;
-                Q.out_cnt[p] = 0;
-                if (Q.out_ovf) Q.out_ovf[p] = 0;
-            } else {
-                Q.out_dist[p] = (uint16_t)gbest;
-                Q.out_cnt[p] = sum;
-                if (Q.out_ovf) Q.out_ovf[p] = (uint8_t)(flag != 0);
+        finish_pair_warp(Q, p, best, sum, flag, lane);
+    }
+}
+
+// Pairs grouped by source (perm sorted by s; sources outside [0, n) last).
+// The sorted pairs are cut into items of kBySourceItem; a CTA takes items
+// in turn and walks each item's runs of pairs with one source s. For a run
+// it puts L(s) into an on-chip hash (slot = hub | distance << 24 | entry
+// index << 40), then each warp answers one pair of the run at a time by
+// streaming L(t), kBySourceUnroll loads in flight per lane, and probing the
+// hash for each hub. L(s) is read once per run instead of once per pair,
+// and no warp waits on a second list. The table has pow2 >= 2|L(s)| slots
+// (at most max_slots, which the host sizes from the largest label), so a
+// probe always ends at an empty slot.
+constexpr int kBySourceItem = 128;
+constexpr int kBySourceUnroll = 8;
+constexpr unsigned long long kEmptySlot = ~0ull;
+
+__global__ void __launch_bounds__(kQueryThreads) k_query_by_source(const QueryArgs Q, uint32_t max_slots) {
+    extern __shared__ unsigned long long tab[];
+    __shared__ int32_t s_src[kBySourceItem];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t items = (Q.q + kBySourceItem - 1) / kBySourceItem;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t kb = item * kBySourceItem;
+        const int m = (int)(Q.q - kb < kBySourceItem ? Q.q - kb : kBySourceItem);
+        if (tid < m) s_src[tid] = __ldg(Q.pairs + 2 * (int64_t)__ldg(Q.perm + kb + tid));
+        __syncthreads();
+        for (int r0 = 0; r0 < m;) {
+            const int32_t s = s_src[r0];
+            int r1 = r0 + 1;
+            while (r1 < m && s_src[r1] == s) ++r1;
+            if (s < 0 || s >= Q.n) {  // the sort puts every invalid source in this bucket
+                for (int r = r0 + tid; r < r1; r += blockDim.x) {
+                    const int64_t p = __ldg(Q.perm + kb + r);
+                    atomicOr(Q.err, 1);
+                    write_fixed(Q, p, PSPC_UNREACHED, 0);
+                }
+                r0 = r1;
+                continue;
             }
+            const int32_t rs = __ldg(Q.rank + s);
+            const int64_t a0 = __ldg(Q.off + rs);
+            const uint32_t la = (uint32_t)(__ldg(Q.off + rs + 1) - a0);
+            uint32_t slots = pow2_ceil(2ull * la);
+            slots = slots < 64u ? 64u : (slots > max_slots ? max_slots : slots);
+            const uint32_t mask = slots - 1;
+            for (uint32_t i = tid; i < slots; i += blockDim.x) tab[i] = kEmptySlot;
+            __syncthreads();
+            for (uint32_t i = tid; i < la; i += blockDim.x) {
+                const uint32_t h = (uint32_t)__ldg(Q.hub + a0 + i);
+                const unsigned long long v = (unsigned long long)h | ((unsigned long long)__ldg(Q.dist + a0 + i) << 24) |
+                                             ((unsigned long long)i << 40);
+                uint32_t slot = hash_hub(h) & mask;
+                for (uint32_t probe = 0; probe < slots; ++probe) {
+                    if (atomicCAS(&tab[slot], kEmptySlot, v) == kEmptySlot) break;
+                    slot = (slot + 1) & mask;
+                }
+            }
+            __syncthreads();
+            for (int r = r0 + w; r < r1; r += kChunkWarps) {
+                const int64_t p = __ldg(Q.perm + kb + r);
+                const int32_t t = __ldg(Q.pairs + 2 * p + 1);
+                if (t < 0 || t >= Q.n) {
+                    if (lane == 0) {
+                        atomicOr(Q.err, 1);
+                        write_fixed(Q, p, PSPC_UNREACHED, 0);
+                    }
+                    continue;
+                }
+                if (t == s) {
+                    if (lane == 0) write_fixed(Q, p, 0, 1);
+                    continue;
+                }
+                const int32_t rt = __ldg(Q.rank + t);
+                const int64_t b0 = __ldg(Q.off + rt);
+                const int64_t lb = __ldg(Q.off + rt + 1) - b0;
+                uint32_t best = 0xFFFFFFFFu;
+                uint64_t sum = 0;
+                uint32_t flag = 0;
+                for (int64_t j0 = 0; j0 < lb; j0 += 32 * kBySourceUnroll) {
+                    uint32_t hb[kBySourceUnroll];
+                    uint16_t db[kBySourceUnroll];
+#pragma unroll
+                    for (int u = 0; u < kBySourceUnroll; ++u) {
+                        const int64_t j = j0 + 32 * u + lane;
+                        hb[u] = j < lb ? (uint32_t)__ldg(Q.hub + b0 + j) : kNoHub;
+                        db[u] = j < lb ? __ldg(Q.dist + b0 + j) : (uint16_t)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kBySourceUnroll; ++u) {
+                        if (hb[u] == kNoHub) continue;
+                        uint32_t slot = hash_hub(hb[u]) & mask;
+                        unsigned long long e = tab[slot];
+                        for (uint32_t probe = 0; e != kEmptySlot && (uint32_t)(e & 0xFFFFFFu) != hb[u] && probe < slots;
+                             ++probe) {
+                            slot = (slot + 1) & mask;
+                            e = tab[slot];
+                        }
+                        if (e == kEmptySlot || (uint32_t)(e & 0xFFFFFFu) != hb[u]) continue;
+                        const uint16_t da = (uint16_t)(e >> 24);
+                        const uint32_t dsum = (uint32_t)(da & 0x7FFF) + (uint32_t)(db[u] & 0x7FFF);
+                        if (dsum > best) continue;
+                        const uint64_t ca = __ldg((const unsigned long long*)Q.cnt + a0 + (uint32_t)(e >> 40));
+                        const uint64_t cb = __ldg((const unsigned long long*)Q.cnt + b0 + j0 + 32 * u + lane);
+                        const uint64_t prod = ca * cb;
+                        const uint32_t tf =
+                            (uint32_t)(da >> 15) | (uint32_t)(db[u] >> 15) | (uint32_t)(__umul64hi(ca, cb) != 0);
+                        if (dsum < best) {
+                            best = dsum;
+                            sum = prod;
+                            flag = tf;
+                        } else {
+                            add_term(sum, flag, prod, tf);
+                        }
+                    }
+                }
+                finish_pair_warp(Q, p, best, sum, flag, lane);
+            }
+            __syncthreads();
+            r0 = r1;
         }
+        __syncthreads();  // s_src is rewritten by the next item
     }
 }
 
@@ -303,8 +439,13 @@ static void prefer_max_shared(const void* fn) {
 
 static std::once_flag g_carveout_once;
 
+constexpr uint32_t kBySourceMaxSlots = 16384;  // 128 KB of table
+
 static void set_query_carveouts() {
     std::call_once(g_carveout_once, [] {
+        prefer_max_shared((const void*)k_query_by_source);
+        cudaFuncSetAttribute((const void*)k_query_by_source, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kBySourceMaxSlots * 8));
         prefer_max_shared((const void*)k_query<8>);
         prefer_max_shared((const void*)k_query<16>);
         prefer_max_shared((const void*)k_query<32>);
@@ -314,13 +455,66 @@ static void set_query_carveouts() {
     });
 }
 
-// Lanes per pair: wide groups for long labels (fewer merge steps), narrow
-// groups for short ones (more pairs in flight per warp).
-// Long labels: warp-staged chunks of 256 entries.
-static int query_group_for(const Index& ix) {
-    if (ix.query_group) return ix.query_group;
+// Table slots the by-source kernel needs for the largest label (0: it does
+// not fit on chip).
+static uint32_t by_source_slots(const Index& ix) {
+    const uint32_t s = pow2_ceil(2ull * (uint64_t)(ix.max_label > 0 ? ix.max_label : 1));
+    return s <= kBySourceMaxSlots ? (s < 64u ? 64u : s) : 0u;
+}
+
+// The query kernel. Automatic choice: by source when the pairs are grouped,
+// L(s) fits on chip and sources repeat often (q >= 64 n: each table build
+// serves many pairs; with fewer pairs per source the staged merge-join,
+// whose L(s) reads mostly hit L2 after the grouping sort, measured faster);
+// otherwise lanes per pair from the label sizes: wide groups for long
+// labels (fewer merge steps), narrow groups for short ones (more pairs in
+// flight per warp), warp-staged chunks of 256 entries for long labels.
+static int query_group_for(const Index& ix, bool grouped, int64_t q) {
+    const bool by_source_ok = grouped && by_source_slots(ix) > 0;
+    if (ix.query_group == PSPC_QUERY_BY_SOURCE && by_source_ok) return PSPC_QUERY_BY_SOURCE;
+    if (ix.query_group && ix.query_group != PSPC_QUERY_BY_SOURCE) return ix.query_group;
+    if (ix.query_group == 0 && by_source_ok && q >= 64 * ix.n) return PSPC_QUERY_BY_SOURCE;
     const double avg = ix.n ? (double)ix.entries / (double)ix.n : 0.0;
     return avg >= 128.0 ? 256 : (avg >= 24.0 ? 16 : 8);
+}
+
+// Launches the query kernel chosen for the index (Q.perm is the grouping
+// sort's order, or NULL). Counts the launch on the index.
+static cudaError_t launch_query(Index& ix, const QueryArgs& Q, cudaStream_t st) {
+    set_query_carveouts();
+    const int G = query_group_for(ix, Q.perm != nullptr, Q.q);
+    int sms = 0, occ = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
+    if (e != cudaSuccess) return e;
+    __atomic_fetch_add(&ix.query_launches, (int64_t)1, __ATOMIC_RELAXED);
+    if (G == PSPC_QUERY_BY_SOURCE) {
+        const uint32_t slots = by_source_slots(ix);
+        const size_t smem = (size_t)slots * 8;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_query_by_source, kQueryThreads, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t items = (Q.q + kBySourceItem - 1) / kBySourceItem;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * std::max(occ, 1)));
+        k_query_by_source<<<grid, kQueryThreads, smem, st>>>(Q, slots);
+        return cudaGetLastError();
+    }
+    const void* fn = G == 8 ? (const void*)k_query<8>
+                     : G == 16 ? (const void*)k_query<16>
+                     : G == 32 ? (const void*)k_query<32>
+                     : G == 64 ? (const void*)k_query_chunked<64>
+                     : G == 128 ? (const void*)k_query_chunked<128>
+                                : (const void*)k_query_chunked<256>;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQueryThreads, 0);
+    if (e != cudaSuccess) return e;
+    const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
+    const int64_t want = (Q.q + per_block - 1) / per_block;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
+    if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
+    else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
+    else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
+    else if (G == 64) k_query_chunked<64><<<grid, kQueryThreads, 0, st>>>(Q);
+    else if (G == 128) k_query_chunked<128><<<grid, kQueryThreads, 0, st>>>(Q);
+    else k_query_chunked<256><<<grid, kQueryThreads, 0, st>>>(Q);
+    return cudaGetLastError();
 }
 
 }  // namespace pspc
@@ -401,28 +595,7 @@ extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q,
         Q.out_cnt = dev_out ? count : d_cnt;
         Q.out_ovf = dev_out ? overflow : d_ovf;
         Q.err = d_err;
-        set_query_carveouts();
-        const int G = query_group_for(ix);
-        const void* fn = G == 8 ? (const void*)k_query<8>
-                         : G == 16 ? (const void*)k_query<16>
-                         : G == 32 ? (const void*)k_query<32>
-                         : G == 64 ? (const void*)k_query_chunked<64>
-                         : G == 128 ? (const void*)k_query_chunked<128>
-                                    : (const void*)k_query_chunked<256>;
-        int sms = 0, occ = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQueryThreads, 0);
-        const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
-        const int64_t want = (q + per_block - 1) / per_block;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
-        __atomic_fetch_add(&h->ix.query_launches, (int64_t)1, __ATOMIC_RELAXED);
-        if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
-        else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
-        else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
-        else if (G == 64) k_query_chunked<64><<<grid, kQueryThreads, 0, st>>>(Q);
-        else if (G == 128) k_query_chunked<128><<<grid, kQueryThreads, 0, st>>>(Q);
-        else k_query_chunked<256><<<grid, kQueryThreads, 0, st>>>(Q);
-        e = cudaGetLastError();
+        e = launch_query(h->ix, Q, st);
     }
     if (e == cudaSuccess && !dev_out) {
         e = cudaMemcpyAsync(dist, d_dist, (size_t)q * 2, cudaMemcpyDeviceToHost, st);
@@ -446,8 +619,8 @@ extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q,
 }
 
 extern "C" int pspc_set_query_group(pspc_index* h, int32_t lanes) {
-    if (!h || !(lanes == 0 || lanes == 8 || lanes == 16 || lanes == 32 || lanes == 64 || lanes == 128 ||
-                lanes == 256))
+    if (!h || !(lanes == 0 || lanes == PSPC_QUERY_BY_SOURCE || lanes == 8 || lanes == 16 || lanes == 32 ||
+                lanes == 64 || lanes == 128 || lanes == 256))
         return PSPC_E_INVAL;
     h->ix.query_group = lanes;
     return PSPC_OK;
@@ -582,28 +755,7 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
             Q.out_cnt = count;
             Q.out_ovf = overflow;
             Q.err = d_err;
-            set_query_carveouts();
-            const int G = query_group_for(ix);
-            const void* fn = G == 8 ? (const void*)k_query<8>
-                             : G == 16 ? (const void*)k_query<16>
-                             : G == 32 ? (const void*)k_query<32>
-                             : G == 64 ? (const void*)k_query_chunked<64>
-                             : G == 128 ? (const void*)k_query_chunked<128>
-                                        : (const void*)k_query_chunked<256>;
-            int sms = 0, occ = 0;
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQueryThreads, 0);
-            const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
-            const int64_t want = (q + per_block - 1) / per_block;
-            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
-            __atomic_fetch_add(&h->ix.query_launches, (int64_t)1, __ATOMIC_RELAXED);
-            if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
-            else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
-            else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
-            else if (G == 64) k_query_chunked<64><<<grid, kQueryThreads, 0, st>>>(Q);
-            else if (G == 128) k_query_chunked<128><<<grid, kQueryThreads, 0, st>>>(Q);
-            else k_query_chunked<256><<<grid, kQueryThreads, 0, st>>>(Q);
-            e = cudaGetLastError();
+            e = launch_query(h->ix, Q, st);
         }
         int herr = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -648,26 +800,5 @@ extern "C" int pspc_query_async(const pspc_index* hc, const int32_t* pairs, int6
     Q.out_cnt = count;
     Q.out_ovf = overflow;
     Q.err = err;
-    set_query_carveouts();
-    const int G = query_group_for(ix);
-    const void* fn = G == 8 ? (const void*)k_query<8>
-                     : G == 16 ? (const void*)k_query<16>
-                     : G == 32 ? (const void*)k_query<32>
-                     : G == 64 ? (const void*)k_query_chunked<64>
-                     : G == 128 ? (const void*)k_query_chunked<128>
-                                : (const void*)k_query_chunked<256>;
-    int sms = 0, occ = 0;
-    PSPC_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device));
-    PSPC_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQueryThreads, 0));
-    const int64_t per_block = G >= 64 ? kChunkWarps : kQueryThreads / G;
-    const int64_t want = (q + per_block - 1) / per_block;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * std::max(occ, 1)));
-    __atomic_fetch_add(&h->ix.query_launches, (int64_t)1, __ATOMIC_RELAXED);
-    if (G == 8) k_query<8><<<grid, kQueryThreads, 0, st>>>(Q);
-    else if (G == 16) k_query<16><<<grid, kQueryThreads, 0, st>>>(Q);
-    else if (G == 32) k_query<32><<<grid, kQueryThreads, 0, st>>>(Q);
-    else if (G == 64) k_query_chunked<64><<<grid, kQueryThreads, 0, st>>>(Q);
-    else if (G == 128) k_query_chunked<128><<<grid, kQueryThreads, 0, st>>>(Q);
-    else k_query_chunked<256><<<grid, kQueryThreads, 0, st>>>(Q);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_query(h->ix, Q, st));
 }

@@ -283,12 +283,48 @@ def test_query_group_invariance(pspc):
         ix = gpu_index(pspc, g, rank)
         pairs = pairs_fn(100000)
         rd, rc, rf, _ = ref.query(pairs)
-        for lanes in (8, 16, 32, 64, 128, 256, 0):
+        for lanes in (8, 16, 32, 64, 128, 256, pspc.PSPC_QUERY_BY_SOURCE, 0):
             ix.set_query_group(lanes)
             d, c, f = gpu_query(ix, pairs)
             assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
         with pytest.raises(pspc.PSPCError):
             ix.set_query_group(12)
+
+
+def test_by_source_skew_repeats_and_overflow(pspc):
+    """The by-source query path (pairs sorted by source, L(s) on chip):
+    one source holding thousands of pairs (runs cut across many items),
+    s = t pairs, every pair of a small graph many times over, and counts
+    that overflow 2^64; answers equal the oracle's and every other variant's."""
+    rng = np.random.default_rng(11)
+    g, rank, pairs_fn = P.workload("ba2000")
+    cases = []
+    hot = np.stack([np.full(5000, 7), rng.integers(0, g.n, 5000)], axis=1)
+    same = np.repeat(rng.integers(0, g.n, 3000)[:, None], 2, axis=1)
+    cases.append((g, rank, np.concatenate([hot, same, pairs_fn(20000)]).astype(np.int32)))
+    dg = G.diamond_chain(65)
+    drank = np.arange(dg.n, dtype=np.int32)
+    allp = np.array([(s, t) for s in range(dg.n) for t in range(dg.n)], np.int32)
+    cases.append((dg, drank, np.concatenate([allp] * 3)))
+    for gg, rk, pairs in cases:
+        pairs = pairs[rng.permutation(len(pairs))]
+        rd, rc, rf, _ = oracle.OracleIndex(gg, rk).query(pairs)
+        ix = gpu_index(pspc, gg, rk)
+        for lanes in (pspc.PSPC_QUERY_BY_SOURCE, 256, 8):
+            ix.set_query_group(lanes)
+            d, c, f = gpu_query(ix, pairs)
+            assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
+            d, c, f = gpu_query(ix, pairs, device=False)
+            assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
+        if gg is dg:
+            assert rf.any()
+        bad = pairs.copy()
+        bad[len(bad) // 2, 0] = gg.n
+        with pytest.raises(pspc.PSPCError) as e:
+            ix.set_query_group(0)
+            gpu_query(ix, bad)
+        assert e.value.code == 1
+        ix.free()
 
 
 @pytest.mark.parametrize("map_kind", [1, 2, 3])
