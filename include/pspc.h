@@ -109,7 +109,8 @@ typedef struct {
     float ms;                  /* device time of the whole level */
     float kernel_ms;           /* device time of the level's gather/merge/
                                   prune/append kernel launches only */
-    int64_t landmark_pruned;   /* candidates the landmark filter dropped
+    int64_t landmark_pruned;   /* candidates the landmark filter dropped */
+    int64_t landmark_proven;   /* candidates the landmarks proved to survive
                                   (the rest went through the label scan) */
 } pspc_level_stat_t;
 

@@ -1048,6 +1048,7 @@ struct Builder {
                 keep.bump = lvl_base[d];
                 keep.unique_total = 0;
                 keep.lmk_pruned = 0;
+                keep.lmk_proven = 0;
                 keep.n_retry = 0;
                 keep.arena_overflow = 0;
                 keep.work_smem = keep.work_global = 0;
@@ -1070,6 +1071,7 @@ struct Builder {
             ls.ms = ms;
             ls.kernel_ms = kernel_ms;
             ls.landmark_pruned = (long long)hstt->lmk_pruned;
+            ls.landmark_proven = (long long)hstt->lmk_proven;
             out.lstats.push_back(ls);
             if (o.verbose)
                 fprintf(stderr, "pspc level %d: raw %lld unique %lld entries %lld active %d (off-chip %d) %.3f ms\n",

@@ -23,7 +23,8 @@
 //      overflow flag takes the entry's flag and the carry: Label Merging).
 //   3. Landmark filter (Section "Landmark-Based Filtering"), when the build
 //      has landmark distances: a candidate h with sd(u,l) + sd(l,h) < d for
-//      a landmark l is pruned at once; the others are compacted and go on.
+//      a landmark l is pruned at once, one with |sd(u,l) - sd(l,h)| >= d
+//      survives at once; the others are compacted and go on.
 //      Prune (rule 2) for every remaining candidate h. A common hub x of
 //      L_<d(u) and L_<d(h) with d_u(x) + d_h(x) < d exists iff some
 //      x in L_k(h), 1 <= k <= d-2, has d_u(x) <= d-1-k (the case k = 0,
@@ -47,7 +48,9 @@ namespace pspc {
 
 constexpr int kProbeUnroll = 4;  // loads in flight per lane in the prune scan
 constexpr int kGatherUnroll = 4; // loads in flight per lane in the pull
-constexpr uint32_t kPrunedBit = 0x80000000u;
+constexpr uint32_t kPrunedBit = 0x80000000u;  // list entry: candidate pruned by rule 2
+constexpr uint32_t kProvenBit = 0x40000000u;  // list entry: survival proven by the landmarks
+constexpr uint32_t kSlotMask = 0x3FFFFFFFu;
 
 // ---------------------------------------------------------------------------
 // Cost (rule 1 prefix per arc) and classification.
@@ -303,6 +306,7 @@ __device__ void prune_candidates(const Map& mp, const uint64_t* __restrict__ seg
         c = tile.shfl(c, 0);
         if (c >= M) break;
         const uint32_t slot = list[c];
+        if (slot & kProvenBit) continue;
         const uint32_t h = ckeys[slot] & kHubMask;
         bool pruned = false;
         for (int k0 = 1; k0 <= d - 2 && !pruned; k0 += G) {
@@ -360,6 +364,7 @@ __device__ void prune_by_level(const Map& mp, const uint64_t* __restrict__ seg,
         c = tile.shfl(c, 0);
         if (c >= M) break;
         const uint32_t slot = list[c];
+        if (slot & kProvenBit) continue;
         const uint32_t h = ckeys[slot] & kHubMask;
         bool pruned = false;
         for (int k = 1; k <= d - 2 && !pruned; ++k) {
@@ -391,58 +396,74 @@ __device__ void prune_by_level(const Map& mp, const uint64_t* __restrict__ seg,
 // so that the long scans of deep levels keep all lanes busy.
 template <class Map>
 __device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, const uint32_t* hub_arena, int64_t n,
-                                          int d, uint32_t* list, const uint32_t* ckeys, int M, int* next) {
-    if (M >= 64) prune_by_level<8>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
-    else if (M >= 16) prune_candidates<16>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
+                                          int d, uint32_t* list, const uint32_t* ckeys, int M, int to_scan,
+                                          int* next) {
+    if (to_scan >= 64) prune_by_level<8>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
+    else if (to_scan >= 16) prune_candidates<16>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
     else prune_candidates<32>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
 }
 
-// Landmark filter (Section "Landmark-Based Filtering"): candidate h of u at
-// level d is pruned at once when some landmark l has sd(u,l) + sd(l,h) < d,
-// for then sd(u,h) < d, which is exactly when rule 2's query over the labels
-// below d prunes it. Distances are bytes (255 = unknown), added with
-// saturation and compared with min(d, 255), so an unknown or saturated sum
-// never prunes. The candidates left are compacted to list[0..kept) in the
-// same order (in rounds of one candidate per thread: every read of a round
-// precedes its writes, and no write reaches past the round's reads).
+// Landmark filter (Section "Landmark-Based Filtering"). For a candidate h
+// of u at level d, rule 2 prunes h exactly when sd(u,h) < d. Each landmark
+// l bounds sd(u,h) from both sides: sd(u,h) <= sd(u,l) + sd(l,h), and
+// sd(u,h) >= |sd(u,l) - sd(l,h)|. An upper bound below d prunes h at once;
+// a lower bound of at least d proves that h survives (it keeps its list
+// entry, marked kProvenBit, and skips the label scan). Distances are bytes
+// (255 = unknown): the sum is taken with saturation and compared with
+// min(d, 255), so an unknown or saturated sum never prunes, and a byte 255
+// on either side gives no lower bound. The candidates not pruned are
+// compacted to list[0..kept) in the same order (in rounds of one candidate
+// per thread: every read of a round precedes its writes, and no write
+// reaches past the round's reads). Returns kept; *n_proven receives the
+// proven ones among them.
 __device__ int landmark_filter(const LevelArgs& A, const uint32_t* s_lmk, int d, uint32_t* list,
-                               const uint32_t* ckeys, int M, int* s_wcnt, int* s_kept) {
+                               const uint32_t* ckeys, int M, int* s_wcnt, int* s_kept, int* n_proven) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t dd = (uint32_t)(d < 255 ? d : 255) * 0x01010101u;
     const int words = A.lmk_stride / 16;
-    int kept = 0;
+    int kept = 0, proven = 0;
     for (int base = 0; base < M; base += kLevelThreads) {
         const int c = base + tid;
         uint32_t slot = 0;
-        bool keep = false;
+        bool keep = false, sure = false;
         if (c < M) {
             slot = list[c];
             const uint4* row = (const uint4*)(A.lmk + (size_t)(ckeys[slot] & kHubMask) * A.lmk_stride);
-            uint32_t hit = 0;
+            uint32_t hit = 0, far = 0;
 #pragma unroll
             for (int w = 0; w < 4; ++w)
                 if (w < words) {
-                    const uint4 b = __ldg(row + w);
-                    hit |= __vcmpltu4(__vaddus4(s_lmk[4 * w + 0], b.x), dd) |
-                           __vcmpltu4(__vaddus4(s_lmk[4 * w + 1], b.y), dd) |
-                           __vcmpltu4(__vaddus4(s_lmk[4 * w + 2], b.z), dd) |
-                           __vcmpltu4(__vaddus4(s_lmk[4 * w + 3], b.w), dd);
+                    const uint4 b4 = __ldg(row + w);
+                    const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t a = s_lmk[4 * w + q], b = bw[q];
+                        hit |= __vcmpltu4(__vaddus4(a, b), dd);
+                        const uint32_t known = ~(__vcmpeq4(a, 0xFFFFFFFFu) | __vcmpeq4(b, 0xFFFFFFFFu));
+                        far |= __vcmpgeu4(__vabsdiffu4(a, b), dd) & known;
+                    }
                 }
             keep = hit == 0u;
+            sure = keep && far != 0u;
         }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        const unsigned bsure = __ballot_sync(0xFFFFFFFFu, sure);
+        if (lane == 0) s_wcnt[warp] = __popc(bal) | (__popc(bsure) << 16);
         __syncthreads();
-        int before = 0, round = 0;
+        int before = 0, round = 0, round_sure = 0;
         for (int w = 0; w < kLevelThreads / 32; ++w) {
-            before += w < warp ? s_wcnt[w] : 0;
-            round += s_wcnt[w];
+            const int v = s_wcnt[w];
+            before += w < warp ? (v & 0xFFFF) : 0;
+            round += v & 0xFFFF;
+            round_sure += v >> 16;
         }
-        if (keep) list[kept + before + __popc(bal & ((1u << lane) - 1u))] = slot;
+        if (keep) list[kept + before + __popc(bal & ((1u << lane) - 1u))] = slot | (sure ? kProvenBit : 0u);
         kept += round;
+        proven += round_sure;
         __syncthreads();
     }
     if (tid == 0) *s_kept = kept;
+    *n_proven = proven;
     return kept;
 }
 
@@ -702,15 +723,18 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         }
 
         // 3. prune rule 2 over levels 1..d-2 of each candidate's label
-        int M_scan = M;
+        int M_scan = M, n_proven = 0;
         if (d >= 3 && !marked && M > 0 && A.lmk) {
-            M_scan = landmark_filter(A, s_lmk, d, list, ckeys, M, s_wcnt, &s_kept);
+            M_scan = landmark_filter(A, s_lmk, d, list, ckeys, M, s_wcnt, &s_kept, &n_proven);
             if (tid == 0 && M_scan < M) atomicAdd(&A.stt->lmk_pruned, (unsigned long long)(M - M_scan));
+            if (tid == 0 && n_proven) atomicAdd(&A.stt->lmk_proven, (unsigned long long)n_proven);
         }
-        if (d >= 3 && !marked && M_scan > 0) {
-            if constexpr (kMap == kMapBitmap) prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, &s_next);
-            else if constexpr (kMap == kMapHash) prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, &s_next);
-            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, &s_next);
+        if (d >= 3 && !marked && M_scan > n_proven) {
+            const int ns = M_scan - n_proven;
+            if constexpr (kMap == kMapBitmap) prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next);
+            else if constexpr (kMap == kMapHash)
+                prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next);
+            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next);
             __syncthreads();
         }
         M = M_scan;  // list[0..M) now holds every candidate that can survive
@@ -729,7 +753,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             for (int c = tid; c < M; c += kLevelThreads) {
                 const uint32_t slot = list[c];
                 if (!(slot & kPrunedBit)) {
-                    const uint32_t h = (ckeys[slot] & kHubMask) - cbase;
+                    const uint32_t h = (ckeys[slot & kSlotMask] & kHubMask) - cbase;
                     atomicOr(&sb[h >> 5], 1u << (h & 31));
                 }
             }
@@ -745,8 +769,9 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                 const unsigned long long b0 = s_base;
                 if (b0 + S <= A.arena_cap) {
                     for (int c = tid; c < M; c += kLevelThreads) {
-                        const uint32_t slot = list[c];
-                        if (slot & kPrunedBit) continue;
+                        const uint32_t e = list[c];
+                        if (e & kPrunedBit) continue;
+                        const uint32_t slot = e & kSlotMask;
                         const uint32_t key = ckeys[slot];
                         const uint32_t h = key & kHubMask;
                         const uint32_t hr = h - cbase;
@@ -759,9 +784,10 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             }
         } else {
             for (int c = tid; c < M; c += kLevelThreads) {
-                const uint32_t slot = list[c];
-                if (!(slot & kPrunedBit))
-                    sortbuf[atomicAdd(&s_nsurv, 1)] = ((unsigned long long)(ckeys[slot] & kHubMask) << 32) | slot;
+                const uint32_t e = list[c];
+                if (!(e & kPrunedBit))
+                    sortbuf[atomicAdd(&s_nsurv, 1)] =
+                        ((unsigned long long)(ckeys[e & kSlotMask] & kHubMask) << 32) | (e & kSlotMask);
             }
             __syncthreads();
             const int S = s_nsurv;

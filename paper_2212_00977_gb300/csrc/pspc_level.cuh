@@ -27,6 +27,7 @@ struct LevelStatus {
     int n_global;
     int n_retry;
     unsigned long long lmk_pruned;  // candidates dropped by the landmark filter
+    unsigned long long lmk_proven;  // candidates the landmarks proved to survive
     int arena_overflow;
     int work_smem;
     int work_global;
