@@ -3,8 +3,9 @@
 This module holds the graph and query generators that both the CUDA path
 and the CPU oracle are fed from. It contains none of the labelling or query
 arithmetic: only graph construction (Barabasi-Albert, R-MAT, perturbed
-grid), symmetrisation into CSR, the degree-descending vertex order the
-workloads use, and uniform query pairs.
+grid), symmetrisation into CSR, the vertex orders the labelling takes as
+input (degree-descending, and the paper's hybrid order of a degree-ordered
+core above a tree-decomposition-ordered fringe), and uniform query pairs.
 
 Graphs are undirected and unweighted, as in the paper's problem statement
 (Section "Preliminaries", Graphs); directed samples are symmetrised, as the
@@ -28,6 +29,8 @@ __all__ = [
     "largest_component",
     "workload",
     "ba_batch",
+    "elimination_order",
+    "hybrid_rank",
 ]
 
 
@@ -202,6 +205,67 @@ def degree_rank(g: Graph, tie: str = "id", seed: int | None = None) -> np.ndarra
     return rank
 
 
+def elimination_order(g: Graph, delta: int | None = None):
+    """Minimum-degree elimination (the tree-decomposition order of the
+    paper's Section "Vertex Order", road network order): repeatedly remove
+    a vertex of smallest current degree (ties by vertex id) and join its
+    remaining neighbours pairwise (fill edges), so the degrees of the
+    neighbours become their true degrees in the reduced graph.
+
+    With ``delta`` given, elimination stops as soon as every remaining
+    vertex has more than ``delta`` neighbours. Returns (eliminated vertex
+    ids in elimination order, remaining vertex ids ascending, degree of
+    every vertex in the reduced graph at the stop, 0 for eliminated ones)."""
+    import heapq
+
+    adj = [set(g.col[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+    heap = [(len(adj[v]), v) for v in range(g.n)]
+    heapq.heapify(heap)
+    gone = np.zeros(g.n, dtype=bool)
+    order = []
+    while heap:
+        dv, v = heapq.heappop(heap)
+        if gone[v] or dv != len(adj[v]):
+            continue  # stale entry
+        if delta is not None and dv > delta:
+            break
+        gone[v] = True
+        order.append(v)
+        nb = list(adj[v])
+        for x in nb:
+            adj[x].discard(v)
+        for i, x in enumerate(nb):
+            for y in nb[i + 1:]:
+                if y not in adj[x]:
+                    adj[x].add(y)
+                    adj[y].add(x)
+        for x in nb:
+            heapq.heappush(heap, (len(adj[x]), x))
+        adj[v] = set()
+    rest = np.flatnonzero(~gone)
+    reduced = np.array([len(a) for a in adj], dtype=np.int64)
+    return np.asarray(order, dtype=np.int64), rest, reduced
+
+
+def hybrid_rank(g: Graph, delta: int | None = 5) -> np.ndarray:
+    """Hybrid vertex order (Section "Vertex Order", Hybrid Vertex Ordering),
+    as a rank array (0 = highest). The fringe is what minimum-degree
+    elimination removes while some vertex has at most ``delta`` neighbours
+    in the reduced graph; the rest is the core. Core vertices rank above
+    all fringe vertices, by degree descending in the reduced graph (the
+    core with its fill edges; ties by degree in G, then by id); fringe
+    vertices follow in reverse elimination order (the last one removed
+    ranks highest), the tree-decomposition order. ``delta=None``
+    eliminates every vertex: the pure tree-decomposition order."""
+    fringe, core, reduced = elimination_order(g, delta)
+    deg = g.degree()
+    core = core[np.lexsort((core, -deg[core], -reduced[core]))]
+    order = np.concatenate([core, fringe[::-1]])
+    rank = np.empty(g.n, dtype=np.int32)
+    rank[order] = np.arange(g.n, dtype=np.int32)
+    return rank
+
+
 def query_pairs(n: int, q: int, seed: int) -> np.ndarray:
     """int32[q, 2] of uniform (s, t) pairs; s == t is allowed."""
     rng = np.random.default_rng(seed)
@@ -253,7 +317,19 @@ def workload(name: str):
       random ties with seed 3; pairs seed 2.
     * ``grid256``: 256x256 grid, 10% of edges deleted, seed 1, largest
       component, random ties with seed 3; pairs seed 2.
+
+    A suffix ``@hybrid<delta>`` or ``@td`` replaces the degree order by the
+    hybrid order with that threshold or by the pure tree-decomposition
+    order (``hybrid_rank``), e.g. ``grid256@td``.
     """
+    if "@" in name:
+        base, how = name.split("@", 1)
+        g, _, pf = workload(base)
+        if how == "td":
+            return g, hybrid_rank(g, None), pf
+        if how.startswith("hybrid") and how[6:].isdigit():
+            return g, hybrid_rank(g, int(how[6:])), pf
+        raise KeyError(name)
     if name == "ba2000":
         g = barabasi_albert(2000, 4, 1)
         rank = degree_rank(g, "id")

@@ -354,3 +354,18 @@ def test_export_vertices_and_hub_column(pspc):
         ix.export_vertices(np.array([2000], np.int32))
     with pytest.raises(pspc.PSPCError):
         ix.hub_column(-1)
+
+
+@pytest.mark.parametrize("name", ["grid64@td", "grid64@hybrid5", "ba2000@hybrid5", "rmat12_ef16@td"])
+def test_order_variants_full_index(pspc, name):
+    """The hybrid and tree-decomposition orders (Section "Vertex Order")
+    give other indexes; each equals the oracle's under the same order."""
+    g, rank, pairs_fn = P.workload(name)
+    ref = oracle.OracleIndex(g, rank)
+    ix = gpu_index(pspc, g, rank)
+    assert_index_equal(ix, ref.export())
+    pairs = pairs_fn(20000)
+    rd, rc, rf, _ = ref.query(pairs)
+    d, c, f = gpu_query(ix, pairs)
+    assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
+    ix.free()
