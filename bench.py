@@ -41,7 +41,7 @@ WORKLOAD_DESC = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="rmat16")
@@ -57,7 +57,7 @@ def dist_info():
 
 
 class ClockSampler:
-    """nvidia-smi sampling (200 ms) of SM clocks and throttle reasons."""
+    """nvidia-smi sampling (100 ms) of SM clocks and throttle reasons."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -73,7 +73,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.gpu)], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "100", "-i", str(self.gpu)], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -287,7 +287,8 @@ def run_ours(args):
                        "queries_per_step": q, "l2": "flushed: 256 MiB device write before every step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "build_ms": T_build / K, "query_ms": T_query / K, "queries_per_s": qps,
-            "entries": entries, "levels": st["levels"],
+            "entries": entries, "levels": st["levels"], "landmarks": st["landmarks"],
+            "landmark_ms": st["landmark_ms"],
             "roofline": {"kernel": "k_level (pull gather + count merge + prune + append)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None,
