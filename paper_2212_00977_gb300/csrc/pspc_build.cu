@@ -494,6 +494,10 @@ struct Builder {
     uint64_t* seg = nullptr;
     int seg_levels_cap = 0;
     uint32_t* cnt_arc = nullptr;
+    uint32_t* arc_lo = nullptr;    // first pulled entry per arc (dense-prefix skip)
+    int32_t* hpre = nullptr;       // dense prefix per vertex
+    bool skip_prefix = false;      // the current level uses arc_lo
+    bool prefix_pays = true;       // the last level that skipped saved enough to go on
     int32_t* arc_src = nullptr;
     int32_t* comp_base = nullptr;  // batches: first rank-space id of each vertex's graph
     int64_t max_comp = 0;          // largest graph (bits per level bitmap)
@@ -524,6 +528,8 @@ struct Builder {
         dfree(cnt_arena, st);
         dfree(seg, st);
         dfree(cnt_arc, st);
+        dfree(arc_lo, st);
+        dfree(hpre, st);
         dfree(arc_src, st);
         dfree(comp_base, st);
         dfree(raw_u, st);
@@ -831,6 +837,7 @@ struct Builder {
         A.rp = rp_r;
         A.col = col_r;
         A.cnt_arc = cnt_arc;
+        A.arc_lo = skip_prefix ? arc_lo : nullptr;
         A.seg = seg;
         A.seg_out = seg + (int64_t)d * n;
         A.hub_arena = hub_arena;
@@ -966,6 +973,8 @@ struct Builder {
         rc = grow_arena(std::max<unsigned long long>(cap0, (unsigned long long)n + 1024), 0);
         if (rc) return rc;
         PSPC_TRY_CUDA(dalloc(&cnt_arc, arcs, st));
+        PSPC_TRY_CUDA(dalloc(&arc_lo, arcs, st));
+        PSPC_TRY_CUDA(dalloc(&hpre, n, st));
         PSPC_TRY_CUDA(dalloc(&raw_u, n, st));
         PSPC_TRY_CUDA(dalloc(&lab_size, n, st));
         PSPC_TRY_CUDA(dalloc(&items, n, st));
@@ -1014,13 +1023,26 @@ struct Builder {
             cudaMemsetAsync(seg + (int64_t)d * n, 0, n * 8, st);
             cudaMemsetAsync(stt, 0, sizeof(LevelStatus), st);
             cudaMemcpyAsync(&stt->bump, &lvl_base[d], 8, cudaMemcpyHostToDevice, st);
-            cudaError_t ce = launch_cost(d, n, arcs, rp_r, col_r, arc_src, seg + (int64_t)(d - 1) * n, hub_arena,
-                                         cnt_arc, raw_u, lab_size, stt, plan.label_limit, glist, items, st,
-                                         &out.launches);
+            // Dense-prefix skip on the shallow levels (the prefix pass reads
+            // d segments per vertex; deep levels of high-diameter graphs gain
+            // little from it).
+            skip_prefix = d >= 3 && d <= kDensePrefixMaxLevel && prefix_pays;
+            cudaError_t ce = cudaSuccess;
+            if (skip_prefix) {
+                ce = launch_dense_prefix(d, n, seg, hub_arena, comp_base, hpre, st);
+                out.launches += 1;
+            }
+            if (ce == cudaSuccess)
+                ce = launch_cost(d, n, arcs, rp_r, col_r, arc_src, seg + (int64_t)(d - 1) * n, hub_arena,
+                                 skip_prefix ? hpre : nullptr, arc_lo, cnt_arc, raw_u, lab_size, stt,
+                                 plan.label_limit, glist, items, st, &out.launches);
             if ((rc = cuda_status(ce))) break;
             if ((rc = read_status())) break;
             if (hstt->n_active == 0) break;
             const long long raw_total = (long long)hstt->raw_total;
+            if (skip_prefix)  // on the graphs measured, the share saved only fell after its first level
+                prefix_pays = (double)hstt->prefix_skipped >=
+                              kDensePrefixMinGain * (double)(hstt->prefix_skipped + hstt->raw_total);
             const long long active_arcs = (long long)hstt->active_arcs;
             // Size the arena for this level before running it: the level
             // adds at most one entry per distinct pulled (u, h), bounded here

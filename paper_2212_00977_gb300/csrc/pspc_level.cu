@@ -2,10 +2,13 @@
 // "Distance Dependency"; Lemma "Propagation"; pruning rules 1 and 2; Label
 // Elimination and Label Merging; cost-function schedule).
 //
-// k_cost_arcs / k_cost_vertices
+// k_dense_prefix / k_cost_arcs / k_cost_vertices
 //   For every arc u->v: how many entries of L_{d-1}(v) have a hub ranked
 //   above u. Level segments are hub-sorted, so rule 1 keeps a prefix, found
-//   by binary search. Per vertex the sum is the pulled-entry count (the
+//   by binary search. The pull of the arc also skips the entries whose hub
+//   lies below u's dense prefix (every rank id up to it is a hub of
+//   L_<d(u), so those entries would be dropped unread by the membership
+//   test of step 2), found by a second binary search. Per vertex the sum is the pulled-entry count (the
 //   paper's cost function); active vertices are bucketed by it so that the
 //   most expensive ones start first.
 //
@@ -62,21 +65,80 @@ __global__ void k_arc_src(const int64_t* __restrict__ rp, int64_t n, int32_t* __
     for (int64_t a = rp[u] + lane; a < rp[u + 1]; a += 32) arc_src[a] = (int32_t)u;
 }
 
-__global__ void k_cost_arcs(int64_t arcs, const int32_t* __restrict__ arc_src, const int32_t* __restrict__ col,
-                            const uint64_t* __restrict__ seg_prev, const uint32_t* __restrict__ hub_arena,
-                            uint32_t* __restrict__ cnt_arc, unsigned long long* __restrict__ raw_u) {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= arcs) return;
-    const uint32_t u = (uint32_t)arc_src[a];
-    const uint64_t s = __ldg(seg_prev + col[a]);
-    const uint32_t* h = hub_arena + seg_start(s);
-    uint32_t lo = 0, hi = seg_len(s);
+// First index of the hub-sorted segment h[0..len) whose hub is >= x.
+__device__ __forceinline__ uint32_t seg_lower_bound(const uint32_t* h, uint32_t len, uint32_t x) {
+    uint32_t lo = 0, hi = len;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if ((__ldg(h + mid) & kHubMask) < u) lo = mid + 1; else hi = mid;
+        if ((__ldg(h + mid) & kHubMask) < x) lo = mid + 1; else hi = mid;
     }
-    cnt_arc[a] = lo;
-    if (lo) atomicAdd(raw_u + u, (unsigned long long)lo);
+    return lo;
+}
+
+__global__ void k_cost_arcs(int64_t arcs, const int32_t* __restrict__ arc_src, const int32_t* __restrict__ col,
+                            const uint64_t* __restrict__ seg_prev, const uint32_t* __restrict__ hub_arena,
+                            const int32_t* __restrict__ hpre, uint32_t* __restrict__ arc_lo,
+                            uint32_t* __restrict__ cnt_arc, unsigned long long* __restrict__ raw_u,
+                            unsigned long long* __restrict__ skipped) {
+    __shared__ unsigned long long s_skip;
+    if (threadIdx.x == 0) s_skip = 0;
+    __syncthreads();
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < arcs) {
+        const uint32_t u = (uint32_t)arc_src[a];
+        const uint64_t s = __ldg(seg_prev + col[a]);
+        const uint32_t* h = hub_arena + seg_start(s);
+        const uint32_t end = seg_lower_bound(h, seg_len(s), u);  // rule 1: hubs ranked above u
+        uint32_t lo = 0;
+        if (hpre) {
+            lo = seg_lower_bound(h, end, (uint32_t)__ldg(hpre + u));
+            arc_lo[a] = lo;
+            if (lo) atomicAdd(&s_skip, (unsigned long long)lo);
+        }
+        cnt_arc[a] = end - lo;
+        if (end > lo) atomicAdd(raw_u + u, (unsigned long long)(end - lo));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_skip) atomicAdd(skipped, s_skip);
+}
+
+// Warp per vertex: a bitmap of the first kDensePrefixWindow ids of u's
+// graph, set for every hub of L_0(u) .. L_{d-1}(u) in that window (the
+// segments are hub-sorted, so each lane stops at the window's end); the
+// first clear bit is the dense prefix.
+constexpr int kPrefixWarps = 8;
+
+__global__ void __launch_bounds__(kPrefixWarps * 32)
+    k_dense_prefix(int d, int64_t n, const uint64_t* __restrict__ seg, const uint32_t* __restrict__ hub_arena,
+                   const int32_t* __restrict__ comp_base, int32_t* __restrict__ hpre) {
+    __shared__ uint32_t bits[kPrefixWarps][kDensePrefixWindow / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t u = (int64_t)blockIdx.x * kPrefixWarps + w;
+    if (u >= n) return;  // the whole warp
+    const uint32_t cb = comp_base ? (uint32_t)__ldg(comp_base + u) : 0u;
+    const uint32_t lim = cb + kDensePrefixWindow;
+    bits[w][lane] = 0u;
+    __syncwarp();
+    for (int l = 0; l < d; ++l) {
+        const uint64_t s = __ldg(seg + (int64_t)l * n + u);
+        const uint32_t len = seg_len(s);
+        const uint32_t* hs = hub_arena + seg_start(s);
+        for (uint32_t i = lane; i < len; i += 32) {
+            const uint32_t x = __ldg(hs + i) & kHubMask;
+            if (x >= lim) break;
+            atomicOr(&bits[w][(x - cb) >> 5], 1u << ((x - cb) & 31));
+        }
+    }
+    __syncwarp();
+    const uint32_t word = bits[w][lane];
+    const unsigned open = __ballot_sync(0xFFFFFFFFu, word != 0xFFFFFFFFu);
+    uint32_t H = lim;
+    if (open) {
+        const int k = __ffs(open) - 1;
+        const uint32_t wk = __shfl_sync(0xFFFFFFFFu, word, k);
+        H = cb + 32u * k + (uint32_t)(__ffs(~wk) - 1);
+    }
+    if (lane == 0) hpre[u] = (int32_t)(H < (uint32_t)u ? H : (uint32_t)u);
 }
 
 __global__ void k_cost_vertices(int64_t n, const int64_t* __restrict__ rp, const uint64_t* __restrict__ seg_prev,
@@ -582,7 +644,9 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             if (tid < nc) {
                 const uint32_t c = __ldg(A.cnt_arc + ca + tid);
                 pfx[tid] = c;
-                st[tid] = c ? seg_start(__ldg(seg_prev + __ldg(A.col + ca + tid))) : 0ull;
+                st[tid] = c ? seg_start(__ldg(seg_prev + __ldg(A.col + ca + tid))) +
+                                  (A.arc_lo ? __ldg(A.arc_lo + ca + tid) : 0u)
+                            : 0ull;
             }
             __syncthreads();
             const long long total = block_excl_scan(pfx, nc, s_wsum);
@@ -827,15 +891,24 @@ cudaError_t launch_arc_src(const int64_t* rp, int64_t n, int32_t* arc_src, cudaS
     return cudaGetLastError();
 }
 
+cudaError_t launch_dense_prefix(int d, int64_t n, const uint64_t* seg, const uint32_t* hub_arena,
+                                const int32_t* comp_base, int32_t* hpre, cudaStream_t st) {
+    k_dense_prefix<<<(unsigned)((n + kPrefixWarps - 1) / kPrefixWarps), kPrefixWarps * 32, 0, st>>>(
+        d, n, seg, hub_arena, comp_base, hpre);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cost(int d, int64_t n, int64_t arcs, const int64_t* rp, const int32_t* col,
                         const int32_t* arc_src, const uint64_t* seg_prev, const uint32_t* hub_arena,
-                        uint32_t* cnt_arc, int64_t* raw_u, int64_t* lab_size, LevelStatus* stt,
-                        int64_t label_limit, int32_t* glist, int32_t* items, cudaStream_t st, int64_t* launches) {
+                        const int32_t* hpre, uint32_t* arc_lo, uint32_t* cnt_arc, int64_t* raw_u,
+                        int64_t* lab_size, LevelStatus* stt, int64_t label_limit, int32_t* glist, int32_t* items,
+                        cudaStream_t st, int64_t* launches) {
     cudaError_t e = cudaMemsetAsync(raw_u, 0, n * 8, st);
     if (e != cudaSuccess) return e;
     if (arcs > 0)
-        k_cost_arcs<<<(unsigned)((arcs + 255) / 256), 256, 0, st>>>(arcs, arc_src, col, seg_prev, hub_arena, cnt_arc,
-                                                                     (unsigned long long*)raw_u);
+        k_cost_arcs<<<(unsigned)((arcs + 255) / 256), 256, 0, st>>>(arcs, arc_src, col, seg_prev, hub_arena, hpre,
+                                                                     arc_lo, cnt_arc, (unsigned long long*)raw_u,
+                                                                     &stt->prefix_skipped);
     k_cost_vertices<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, rp, seg_prev, raw_u, lab_size, stt, label_limit,
                                                                   glist);
     k_bucket_base<<<1, 32, 0, st>>>(stt);

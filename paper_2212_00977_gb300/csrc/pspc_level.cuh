@@ -26,6 +26,7 @@ struct LevelStatus {
     int n_smem;
     int n_global;
     int n_retry;
+    unsigned long long prefix_skipped;  // rule-1 entries skipped below the dense prefixes
     unsigned long long lmk_pruned;  // candidates dropped by the landmark filter
     unsigned long long lmk_proven;  // candidates the landmarks proved to survive
     int arena_overflow;
@@ -43,6 +44,7 @@ struct LevelArgs {
     const int64_t* rp;
     const int32_t* col;
     const uint32_t* cnt_arc;
+    const uint32_t* arc_lo;  // first pulled entry of each arc's segment (dense-prefix skip), or NULL
     const uint64_t* seg;  // [levels][n]
     uint64_t* seg_out;    // row d
     uint32_t* hub_arena;
@@ -124,10 +126,22 @@ int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t
 
 // Launchers (pspc_level.cu). Each returns a CUDA error code of the launch.
 cudaError_t launch_arc_src(const int64_t* rp, int64_t n, int32_t* arc_src, cudaStream_t st);
+// Dense prefix of every vertex (k_dense_prefix): hpre[u] = the smallest rank
+// id x >= (first id of u's graph) not in L_<d(u), at most u, looking at the
+// first kDensePrefixWindow ids. Every pulled entry whose hub is below it is
+// in L_<d(u), so the membership filter would drop it; the cost pass then
+// starts each arc's pull after those entries.
+constexpr int kDensePrefixWindow = 1024;
+constexpr int kDensePrefixMaxLevel = 8;  // deeper levels: no skip (cost grows with d)
+constexpr double kDensePrefixMinGain = 0.10;  // stop skipping once it saves less than this share of a level's pulls
+cudaError_t launch_dense_prefix(int d, int64_t n, const uint64_t* seg, const uint32_t* hub_arena,
+                                const int32_t* comp_base, int32_t* hpre, cudaStream_t st);
+// hpre NULL: no skip (arc_lo is not written).
 cudaError_t launch_cost(int d, int64_t n, int64_t arcs, const int64_t* rp, const int32_t* col,
                         const int32_t* arc_src, const uint64_t* seg_prev, const uint32_t* hub_arena,
-                        uint32_t* cnt_arc, int64_t* raw_u, int64_t* lab_size, LevelStatus* stt,
-                        int64_t label_limit, int32_t* glist, int32_t* items, cudaStream_t st, int64_t* launches);
+                        const int32_t* hpre, uint32_t* arc_lo, uint32_t* cnt_arc, int64_t* raw_u,
+                        int64_t* lab_size, LevelStatus* stt, int64_t label_limit, int32_t* glist, int32_t* items,
+                        cudaStream_t st, int64_t* launches);
 cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy);
 cudaError_t launch_level(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,
                          cudaStream_t st);
