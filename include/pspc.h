@@ -101,7 +101,9 @@ typedef struct {
 
 /* Per-level counters of the last build (level d = distance d). */
 typedef struct {
-    int64_t raw_candidates;    /* pulled entries (h, d-1, c) with h above u */
+    int64_t raw_candidates;    /* pulled entries (h, d-1, c) with h above u
+                                  (rule 1), including those below u's dense
+                                  prefix that the kernel skips unread */
     int64_t unique_candidates; /* distinct (u, h) after count merging */
     int64_t entries;           /* survivors appended as level d */
     int64_t active_vertices;   /* vertices with at least one pulled entry */

@@ -1085,7 +1085,7 @@ struct Builder {
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&ms, e0, e1);
             pspc_level_stat_t ls{};
-            ls.raw_candidates = raw_total;
+            ls.raw_candidates = raw_total + (long long)hstt->prefix_skipped;
             ls.unique_candidates = (long long)hstt->unique_total;
             ls.entries = added;
             ls.active_vertices = hstt->n_active;

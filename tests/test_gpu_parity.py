@@ -369,3 +369,43 @@ def test_order_variants_full_index(pspc, name):
     d, c, f = gpu_query(ix, pairs)
     assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
     ix.free()
+
+
+def _level_counts_from_oracle(g, rank):
+    """Per level d >= 2, from the oracle's index and the graph alone: the
+    pulled entries of rule 1 (for every arc u->v, the entries (h, d-1, c) of
+    L(v) with h ranked above u) and the entries at distance d."""
+    lab = oracle.OracleIndex(g, rank).export()
+    n = g.n
+    rank = np.asarray(rank, np.int64)
+    owner = np.repeat(np.arange(n), np.diff(lab.off))
+    orank = rank[owner]
+    hrank = rank[lab.hub.astype(np.int64)]
+    dist = (lab.dist & 0x7FFF).astype(np.int64)
+    src = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    ur, vr = rank[src], rank[g.col.astype(np.int64)]
+    out = {}
+    for d in range(2, int(dist.max()) + 2):
+        keys = np.sort(orank[dist == d - 1] * n + hrank[dist == d - 1])
+        raw = int((np.searchsorted(keys, vr * n + ur) - np.searchsorted(keys, vr * n)).sum())
+        out[d] = (raw, int((dist == d).sum()))
+    return out
+
+
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_ef16", "grid32"])
+def test_level_counters_match_independent_count(pspc, name):
+    """The per-level counters that the roofline's algorithmic bytes come
+    from (pulled entries under rule 1, appended entries) equal a count made
+    from the oracle's index, with the dense-prefix skip and the landmark
+    filter on."""
+    g, rank, _ = P.workload(name)
+    want = _level_counts_from_oracle(g, rank)
+    ix = gpu_index(pspc, g, rank)
+    ls = ix.level_stats()
+    for d, (raw, ent) in want.items():
+        if d - 1 < len(ls):
+            got = ls[d - 1]
+            assert (got["raw_candidates"], got["entries"]) == (raw, ent), d
+        else:
+            assert raw == 0 and ent == 0, d
+    ix.free()
