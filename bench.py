@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ORACLE_SAMPLE_HUBS = 320  # bounded CPU sample: the 320 highest-ranked hubs
+REFERENCE_BUDGET_S = 150.0  # whole --impl reference run, warm-up included
 WORKLOAD_DESC = {
     "rmat16": ("R-MAT scale 16 (65,536 vertices), edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
                "seed 1, symmetrised, self-loops and duplicates removed, degree-descending rank "
@@ -175,16 +176,23 @@ def run_reference(args):
     import pspc_inputs as P
 
     g, rank, _ = P.workload(args.workload)
-    for _ in range(args.warmup):
-        cpu_baseline(g, rank)
+    # Each step labels the top `hubs` hubs. The count is sized during the
+    # warm-up steps so that the whole run takes about REFERENCE_BUDGET_S: the
+    # labeler's time grows about with the square of the hubs it has done
+    # (each new hub's search queries the labels built so far).
+    per_step = max(0.5, min(12.0, REFERENCE_BUDGET_S / max(args.warmup + args.steps, 1)))
+    hubs = 32
+    for _ in range(max(args.warmup, 1)):
+        _, t = cpu_baseline(g, rank, hubs=hubs)
+        hubs = int(max(8, min(ORACLE_SAMPLE_HUBS, 4 * hubs, hubs * (per_step / max(t, 1e-3)) ** 0.5)))
     ent, times = 0, []
     for _ in range(args.steps):
-        e, dt = cpu_baseline(g, rank)
+        e, dt = cpu_baseline(g, rank, hubs=hubs)
         ent = e
         times.append(dt)
     T = sum(times)
     value = ent * len(times) / T
-    sample = (f"hub-pushing labeler (C, 1 thread) over the {ORACLE_SAMPLE_HUBS} highest-ranked hubs of "
+    sample = (f"hub-pushing labeler (C, 1 thread) over the {hubs} highest-ranked hubs of "
               f"the {args.workload} graph: {ent} of its label entries per step")
     line = {"impl": "reference", "metric": "label entries/s (index build)", "value": value, "unit": "entries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
