@@ -97,6 +97,16 @@ typedef struct {
                                 once when sd(u,l) + sd(l,h) < d for some
                                 landmark l. 0 = default (K = 32), -1 = off,
                                 1..64 = K. Results do not depend on it */
+    int32_t reduce_shell;    /* 1: reduction by 1-shell (Section "Index
+                                Size Reduction"): vertices of degree 1 are
+                                peeled repeatedly, the index is built on the
+                                rest (the core), and a peeled vertex is
+                                answered through the core vertex its tree
+                                hangs from. pspc_query gives the same
+                                answers; pspc_query_async, _noalloc, export,
+                                hub_column and landmarks are not available
+                                on such an index (PSPC_E_INVAL). pspc_build
+                                only */
 } pspc_opts;
 
 /* Per-level counters of the last build (level d = distance d). */
@@ -131,6 +141,8 @@ typedef struct {
     float build_ms;      /* device time of pspc_build, input checks included */
     int32_t landmarks;   /* landmarks per graph used by the build (0: none) */
     float landmark_ms;   /* device time of the landmark BFS within build_ms */
+    int64_t shell_vertices; /* vertices peeled by reduce_shell (their labels
+                               are not stored; entries counts the core's) */
 } pspc_stats_t;
 
 /* One graph of a batch: symmetric CSR as in pspc_csr, plus its order. */

@@ -20,6 +20,7 @@
 
 #include "pspc_internal.cuh"
 #include "pspc_level.cuh"
+#include "pspc_shell.cuh"
 
 namespace pspc {
 
@@ -1279,12 +1280,88 @@ static int run_build(const pspc_opts* opts, pspc_index** out, void* stream, int3
     return PSPC_OK;
 }
 
+// Reduction by 1-shell: peel G, build the index of the core (an ordinary
+// index over core ids), and wrap it with the per-vertex roots and depths.
+static int build_reduced(const pspc_csr* g, const int32_t* rank, const pspc_opts* opts, pspc_index** out,
+                         void* stream) {
+    Builder B;
+    B.st = (cudaStream_t)stream;
+    fill_defaults(B.o, opts);
+    if (!pow2_in(B.o.cand_capacity, 1024, 16384) || !pow2_in(B.o.label_capacity, 1024, 16384) || !opts_ok(B.o))
+        return PSPC_E_INVAL;
+    PSPC_TRY_CUDA(cudaGetDevice(&B.dev));
+    cudaEvent_t t0, t1;
+    PSPC_TRY_CUDA(cudaEventCreate(&t0));
+    PSPC_TRY_CUDA(cudaEventCreate(&t1));
+    cudaEventRecord(t0, B.st);
+    int rc = B.stage_inputs(g, rank);
+    if (!rc) rc = B.validate();
+    ShellParts P;
+    if (!rc) rc = shell_reduce(B.n, B.rp, B.col, B.rank, P, B.st, &B.out.launches);
+    pspc_index* core = nullptr;
+    if (!rc) {
+        pspc_csr cg;
+        cg.n = P.n_core;
+        cg.row_ptr = P.rp;
+        cg.col = P.col;
+        pspc_opts co = B.o;
+        co.reduce_shell = 0;
+        rc = pspc_build(&cg, P.rank, &co, &core, stream);
+    }
+    shell_free(P, B.st);
+    pspc_index* h = nullptr;
+    if (!rc) {
+        cudaEventRecord(t1, B.st);
+        cudaError_t e = cudaEventSynchronize(t1);
+        h = new (std::nothrow) pspc_index;
+        if (e != cudaSuccess) rc = cuda_status(e);
+        else if (!h) rc = PSPC_E_NOMEM;
+    }
+    if (rc) {
+        if (core) pspc_free(core);
+        delete h;
+        dfree(P.parent, B.st);
+        dfree(P.root, B.st);
+        dfree(P.depth, B.st);
+        dfree(P.core_id, B.st);
+    } else {
+        Index& ix = h->ix;
+        const Index& c = core->ix;
+        ix.device = c.device;
+        ix.n = B.n;
+        ix.arcs = B.arcs;
+        ix.entries = c.entries;
+        ix.max_label = c.max_label;
+        ix.levels = c.levels;
+        ix.overflow_entries = c.overflow_entries;
+        ix.launches = B.out.launches + c.launches;
+        ix.lstats = c.lstats;
+        ix.lmk_k = c.lmk ? c.lmk_k : 0;
+        ix.lmk_ms = c.lmk_ms;
+        cudaEventElapsedTime(&ix.build_ms, t0, t1);
+        ix.core = core;
+        ix.sh_core = P.core_id;
+        ix.sh_root = P.root;
+        ix.sh_depth = P.depth;
+        ix.sh_parent = P.parent;
+        ix.shell_vertices = P.removed;
+        *out = h;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return rc;
+}
+
 extern "C" int pspc_build(const pspc_csr* g, const int32_t* rank, const pspc_opts* opts, pspc_index** out,
                           void* stream) {
     if (!out) return PSPC_E_INVAL;
     *out = nullptr;
     if (!g || !rank || !g->row_ptr) return PSPC_E_INVAL;
     if (g->n < 1 || g->n > kMaxVertices) return PSPC_E_INVAL;
+    if (opts && opts->reduce_shell) {
+        if (opts->reduce_shell != 1) return PSPC_E_INVAL;
+        return build_reduced(g, rank, opts, out, stream);
+    }
     return run_build(opts, out, stream, 1, [&](Builder& B) { return B.stage_inputs(g, rank); });
 }
 
@@ -1292,6 +1369,6 @@ extern "C" int pspc_build_batch(const pspc_graph* graphs, int32_t k, const pspc_
                                 void* stream) {
     if (!out) return PSPC_E_INVAL;
     *out = nullptr;
-    if (!graphs || k < 1) return PSPC_E_INVAL;
+    if (!graphs || k < 1 || (opts && opts->reduce_shell)) return PSPC_E_INVAL;
     return run_build(opts, out, stream, k, [&](Builder& B) { return B.stage_batch(graphs, k); });
 }

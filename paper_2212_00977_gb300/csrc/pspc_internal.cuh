@@ -10,6 +10,8 @@
 
 #include "pspc.h"
 
+struct pspc_index;
+
 namespace pspc {
 
 // Vertex and hub ids are rank positions (0 = highest rank) inside the
@@ -60,6 +62,16 @@ struct Index {
     int32_t lmk_k = 0;        // landmarks per graph
     int32_t lmk_stride = 0;   // bytes per row (lmk_k rounded up to 16)
     float lmk_ms = 0.f;       // device time of the landmark BFS
+    // 1-shell reduction: when `core` is set, the labels are those of the
+    // 2-core, held by `core` (an index over core ids), and every vertex of G
+    // (caller ids) has its core id (-1 if peeled), its root in the core, its
+    // depth below the root and its parent towards it (-1 in the core).
+    pspc_index* core = nullptr;
+    int32_t* sh_core = nullptr;
+    int32_t* sh_root = nullptr;
+    int32_t* sh_depth = nullptr;
+    int32_t* sh_parent = nullptr;
+    int64_t shell_vertices = 0;
     std::vector<pspc_level_stat_t> lstats;
 };
 

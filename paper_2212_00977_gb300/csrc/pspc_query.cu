@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "pspc_internal.cuh"
+#include "pspc_shell.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -521,10 +522,83 @@ static cudaError_t launch_query(Index& ix, const QueryArgs& Q, cudaStream_t st) 
 
 using namespace pspc;
 
+// A query batch on an index built with the 1-shell reduction: pairs with
+// s = t or a common root are answered by the tree path; the rest become
+// the pairs of their roots in core ids, go through pspc_query on the core
+// index, and get their depths added.
+static int query_reduced(const Index& ix, const int32_t* pairs, int64_t q, uint16_t* dist, uint64_t* count,
+                         uint8_t* overflow, cudaStream_t st) {
+    const bool dev_in = is_device_ptr(pairs), dev_out = is_device_ptr(dist);
+    if (dev_out != is_device_ptr(count) || (overflow && dev_out != is_device_ptr(overflow))) return PSPC_E_INVAL;
+    int32_t *d_pairs = nullptr, *cpairs = nullptr, *extra = nullptr;
+    uint16_t *d_dist = nullptr, *cd = nullptr;
+    uint64_t *d_cnt = nullptr, *cc = nullptr;
+    uint8_t *d_ovf = nullptr, *co = nullptr;
+    int* d_err = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = dev_alloc(p, bytes, st);
+    };
+    alloc((void**)&d_err, sizeof(int));
+    if (!dev_in) alloc((void**)&d_pairs, (size_t)q * 8);
+    if (!dev_out) {
+        alloc((void**)&d_dist, (size_t)q * 2);
+        alloc((void**)&d_cnt, (size_t)q * 8);
+        alloc((void**)&d_ovf, (size_t)q);
+    }
+    alloc((void**)&cpairs, (size_t)q * 8);
+    alloc((void**)&extra, (size_t)q * 4);
+    alloc((void**)&cd, (size_t)q * 2);
+    alloc((void**)&cc, (size_t)q * 8);
+    alloc((void**)&co, (size_t)q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess && !dev_in) e = cudaMemcpyAsync(d_pairs, pairs, (size_t)q * 8, cudaMemcpyHostToDevice, st);
+    const int32_t* pin = dev_in ? pairs : d_pairs;
+    uint16_t* od = dev_out ? dist : d_dist;
+    uint64_t* oc = dev_out ? count : d_cnt;
+    uint8_t* oo = dev_out ? overflow : d_ovf;
+    if (e == cudaSuccess) e = launch_shell_pairs(ix, pin, q, cpairs, extra, od, oc, oo, d_err, st);
+    int rc = PSPC_OK;
+    if (e == cudaSuccess) rc = pspc_query(ix.core, cpairs, q, cd, cc, co, st);
+    if (e == cudaSuccess && rc == PSPC_OK) e = launch_shell_combine(q, extra, cd, cc, co, od, oc, oo, d_err, st);
+    if (e == cudaSuccess && rc == PSPC_OK && !dev_out) {
+        e = cudaMemcpyAsync(dist, d_dist, (size_t)q * 2, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(count, d_cnt, (size_t)q * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && overflow)
+            e = cudaMemcpyAsync(overflow, d_ovf, (size_t)q, cudaMemcpyDeviceToHost, st);
+    }
+    int herr = 0;
+    if (e == cudaSuccess && rc == PSPC_OK) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_status(e);
+    else if (rc == PSPC_OK && (herr & 1)) rc = PSPC_E_INVAL;
+    else if (rc == PSPC_OK && (herr & 2)) rc = PSPC_E_DIST;
+    dev_free(d_err, st);
+    dev_free(d_pairs, st);
+    dev_free(d_dist, st);
+    dev_free(d_cnt, st);
+    dev_free(d_ovf, st);
+    dev_free(cpairs, st);
+    dev_free(extra, st);
+    dev_free(cd, st);
+    dev_free(cc, st);
+    dev_free(co, st);
+    return rc;
+}
+
 extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q, uint16_t* dist, uint64_t* count,
                           uint8_t* overflow, void* stream) {
     if (!hc || q < 0) return PSPC_E_INVAL;
     if (q == 0) return PSPC_OK;
+    if (hc->ix.core) {
+        if (!pairs || !dist || !count) return PSPC_E_INVAL;
+        int prev = 0;
+        cudaGetDevice(&prev);
+        if (prev != hc->ix.device) PSPC_TRY_CUDA(cudaSetDevice(hc->ix.device));
+        const int rc = query_reduced(hc->ix, pairs, q, dist, count, overflow, (cudaStream_t)stream);
+        if (prev != hc->ix.device) cudaSetDevice(prev);
+        return rc;
+    }
     pspc_index* h = const_cast<pspc_index*>(hc);  // only the launch counter changes
     if (!pairs || !dist || !count) return PSPC_E_INVAL;
     const Index& ix = h->ix;
@@ -623,6 +697,7 @@ extern "C" int pspc_set_query_group(pspc_index* h, int32_t lanes) {
                 lanes == 64 || lanes == 128 || lanes == 256))
         return PSPC_E_INVAL;
     h->ix.query_group = lanes;
+    if (h->ix.core) h->ix.core->ix.query_group = lanes;  // the core index runs the queries
     return PSPC_OK;
 }
 
@@ -707,7 +782,7 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
                                   uint64_t* count, uint8_t* overflow, void* stream) {
     if (!hc || q < 0) return PSPC_E_INVAL;
     if (q == 0) return PSPC_OK;
-    if (!pairs || !dist || !count) return PSPC_E_INVAL;
+    if (!pairs || !dist || !count || hc->ix.core) return PSPC_E_INVAL;
     pspc_index* h = const_cast<pspc_index*>(hc);  // only the launch counter changes
     const Index& ix = h->ix;
     // Scratch layout: error flag | n+2 source bins | q pair indices.
@@ -775,7 +850,7 @@ extern "C" int pspc_query_async(const pspc_index* hc, const int32_t* pairs, int6
                                 uint64_t* count, uint8_t* overflow, int32_t* err, void* stream) {
     if (!hc || q < 0 || q >= ((int64_t)1 << 40)) return PSPC_E_INVAL;
     if (q == 0) return PSPC_OK;
-    if (!pairs || !dist || !count || !err) return PSPC_E_INVAL;
+    if (!pairs || !dist || !count || !err || hc->ix.core) return PSPC_E_INVAL;
     pspc_index* h = const_cast<pspc_index*>(hc);  // only the launch counter changes
     const Index& ix = h->ix;
     int cur = 0;

@@ -175,7 +175,12 @@ extern "C" void pspc_free(pspc_index* h) {
     dev_free(ix.dist, 0);
     dev_free(ix.cnt, 0);
     dev_free(ix.lmk, 0);
+    dev_free(ix.sh_core, 0);
+    dev_free(ix.sh_root, 0);
+    dev_free(ix.sh_depth, 0);
+    dev_free(ix.sh_parent, 0);
     cudaStreamSynchronize(0);
+    if (ix.core) pspc_free(ix.core);
     cudaSetDevice(prev);
     delete h;
 }
@@ -197,11 +202,19 @@ extern "C" int pspc_stats(const pspc_index* h, pspc_stats_t* s) {
     s->build_ms = ix.build_ms;
     s->landmarks = ix.lmk ? ix.lmk_k : 0;
     s->landmark_ms = ix.lmk_ms;
+    if (ix.core) {  // labels, landmarks and their sizes are the core's
+        pspc_stats_t c;
+        pspc_stats(ix.core, &c);
+        s->index_bytes = c.index_bytes + ix.n * 16;
+        s->landmarks = c.landmarks;
+        s->query_kernel_launches += c.query_kernel_launches;
+        s->shell_vertices = ix.shell_vertices;
+    }
     return PSPC_OK;
 }
 
 extern "C" int pspc_landmarks(const pspc_index* h, int32_t* k, uint8_t* dist) {
-    if (!h || !k) return PSPC_E_INVAL;
+    if (!h || !k || h->ix.core) return PSPC_E_INVAL;
     const Index& ix = h->ix;
     *k = ix.lmk ? ix.lmk_k : 0;
     if (!dist || !ix.lmk) return PSPC_OK;
@@ -240,7 +253,7 @@ extern "C" int pspc_level_stats(const pspc_index* h, pspc_level_stat_t* out, int
 
 extern "C" int pspc_export(const pspc_index* h, int64_t* off, int32_t* hub, uint16_t* dist,
                            uint64_t* cnt, uint8_t* ovf) {
-    if (!h || !off || (h->ix.entries > 0 && (!hub || !dist || !cnt || !ovf))) return PSPC_E_INVAL;
+    if (!h || h->ix.core || !off || (h->ix.entries > 0 && (!hub || !dist || !cnt || !ovf))) return PSPC_E_INVAL;
     const Index& ix = h->ix;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -345,7 +358,7 @@ __global__ void k_vert_gather(int64_t k, const int32_t* __restrict__ verts, int6
 }  // namespace pspc
 
 extern "C" int pspc_hub_column(const pspc_index* h, int32_t w, uint16_t* dist, uint64_t* cnt, uint8_t* ovf) {
-    if (!h || !dist || !cnt || !ovf) return PSPC_E_INVAL;
+    if (!h || h->ix.core || !dist || !cnt || !ovf) return PSPC_E_INVAL;
     const Index& ix = h->ix;
     if (w < 0 || w >= ix.n) return PSPC_E_INVAL;
     int prev = 0;
@@ -379,7 +392,7 @@ extern "C" int pspc_hub_column(const pspc_index* h, int32_t w, uint16_t* dist, u
 
 extern "C" int pspc_export_vertices(const pspc_index* h, const int32_t* verts, int64_t k, int64_t* off, int32_t* hub,
                                     uint16_t* dist, uint64_t* cnt, uint8_t* ovf) {
-    if (!h || k < 0 || (k > 0 && !verts) || !off) return PSPC_E_INVAL;
+    if (!h || h->ix.core || k < 0 || (k > 0 && !verts) || !off) return PSPC_E_INVAL;
     const Index& ix = h->ix;
     if (k == 0) {
         off[0] = 0;
