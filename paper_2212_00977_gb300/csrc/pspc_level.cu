@@ -50,6 +50,8 @@ namespace cg = cooperative_groups;
 namespace pspc {
 
 constexpr int kProbeUnroll = 4;  // loads in flight per lane in the prune scan
+constexpr uint32_t kSegCacheMinWords = 1024;  // narrowest useful level cache (32K ids)
+constexpr uint32_t kSegCacheMaxWords = 8192;  // widest (the off-chip tables can be far larger)
 constexpr int kGatherUnroll = 4; // loads in flight per lane in the pull
 constexpr uint32_t kPrunedBit = 0x80000000u;  // list entry: candidate pruned by rule 2
 constexpr uint32_t kProvenBit = 0x40000000u;  // list entry: survival proven by the landmarks
@@ -251,8 +253,18 @@ struct SegMap {
     const uint32_t* hub_arena;
     int64_t n, u;
     int d;
+    // Optional on-chip cache: one bitmap per level 1..d-1 over the ids
+    // base .. base + 32*cwords - 1 (the highest-ranked hubs, which hold
+    // most label entries of power-law graphs); NULL when not built.
+    const uint32_t* cache;
+    uint32_t cwords;
+    uint32_t base;
     __device__ bool in_level(uint32_t x, int l) const {
         if (l < 1) return false;  // level 0 is u itself
+        if (cache && x - base < 32u * cwords) {
+            const uint32_t r = x - base;
+            return (cache[(uint32_t)(l - 1) * cwords + (r >> 5)] >> (r & 31)) & 1u;
+        }
         const uint64_t s = __ldg(seg + (int64_t)l * n + u);
         const uint32_t* h = hub_arena + seg_start(s);
         uint32_t lo = 0, hi = seg_len(s);
@@ -597,6 +609,9 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         sm.n = n;
         sm.u = u;
         sm.d = d;
+        sm.cache = nullptr;
+        sm.cwords = 0;
+        sm.base = cbase;
         if (kMap == kMapSeg) {
         } else if (kMap == kMapBitmap) {
             bm.bits = (uint32_t*)mapr;
@@ -636,6 +651,33 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             }
         }
         __syncthreads();
+
+        // 1b. segment-search map: cache the levels of u on chip over the
+        // first ids that the table region can hold (the region is free
+        // until the prune step is done). Each thread walks hub-sorted
+        // segments, so it stops at the first hub beyond the window.
+        if (kMap == kMapSeg && d > 1) {
+            uint32_t cw = (uint32_t)((L.list - L.map) / 4) / (uint32_t)(d - 1);
+            cw = cw < kSegCacheMaxWords ? cw : kSegCacheMaxWords;
+            if (cw >= kSegCacheMinWords) {
+                uint32_t* cache = (uint32_t*)mapr;
+                for (uint32_t i = tid; i < (uint32_t)(d - 1) * cw; i += kLevelThreads) cache[i] = 0u;
+                __syncthreads();
+                for (int l = 1; l < d; ++l) {
+                    const uint64_t s = __ldg(A.seg + (int64_t)l * n + u);
+                    const uint32_t len = seg_len(s);
+                    const uint32_t* hs = A.hub_arena + seg_start(s);
+                    for (uint32_t i = tid; i < len; i += kLevelThreads) {
+                        const uint32_t r = (__ldg(hs + i) & kHubMask) - cbase;
+                        if (r >= 32u * cw) break;
+                        atomicOr(&cache[(uint32_t)(l - 1) * cw + (r >> 5)], 1u << (r & 31));
+                    }
+                }
+                __syncthreads();
+                sm.cache = cache;
+                sm.cwords = cw;
+            }
+        }
 
         // 2. pull with the membership filter, merged per hub
         const int64_t a0 = A.rp[u], a1 = A.rp[u + 1];
