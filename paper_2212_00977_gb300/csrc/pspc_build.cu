@@ -406,6 +406,15 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_merge(const FinArgs F)
         const int64_t o0 = F.off[u];
         const int T = (int)(F.off[u + 1] - o0);
         if (T > kFinSmemKeys) continue;  // uniform: sorted by the off-chip pass
+        if (T == 1) {  // only (u, 0, 1): an isolated vertex, no merge
+            if (tid == 0) {
+                const uint64_t s = __ldg(F.seg + u);
+                F.hub[o0] = (int32_t)(__ldg(F.hub_arena + seg_start(s)) & kHubMask);
+                F.dist[o0] = 0;
+                F.cnt[o0] = __ldg((const unsigned long long*)F.cnt_arena + seg_start(s));
+            }
+            continue;
+        }
         if (tid < L) {
             const uint64_t s = __ldg(F.seg + (int64_t)tid * F.n + u);
             s_st[tid] = seg_start(s);
@@ -428,6 +437,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_merge(const FinArgs F)
             while (s_off[l + 1] <= i) ++l;
             const uint32_t w = s_hub[i];
             const uint32_t h = w & kHubMask;
+            const unsigned long long c = __ldg((const unsigned long long*)F.cnt_arena + s_st[l] + (i - s_off[l]));
             int pos = i - s_off[l];
             for (int l2 = 0; l2 < L; ++l2) {
                 if (l2 == l) continue;
@@ -442,7 +452,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_merge(const FinArgs F)
             novf += ovf;
             F.hub[o0 + pos] = (int32_t)h;
             F.dist[o0 + pos] = (uint16_t)(l | (ovf << 15));
-            F.cnt[o0 + pos] = __ldg((const unsigned long long*)F.cnt_arena + s_st[l] + (i - s_off[l]));
+            F.cnt[o0 + pos] = c;
         }
         __syncthreads();
     }
@@ -839,6 +849,7 @@ struct Builder {
         A.col = col_r;
         A.cnt_arc = cnt_arc;
         A.arc_lo = skip_prefix ? arc_lo : nullptr;
+        A.hpre = skip_prefix ? hpre : nullptr;
         A.seg = seg;
         A.seg_out = seg + (int64_t)d * n;
         A.hub_arena = hub_arena;

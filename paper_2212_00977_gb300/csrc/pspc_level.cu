@@ -774,11 +774,14 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                 const int nc = (int)(len1 - c0 < (uint32_t)kArcChunk ? len1 - c0 : (uint32_t)kArcChunk);
                 if (tid < nc) {
                     const uint32_t x = __ldg(xs + c0 + tid) & kHubMask;
+                    // below u's dense prefix every id is in L_<3(u), so no
+                    // candidate: start the walk at the prefix when it is past x
+                    const uint32_t from = A.hpre && (uint32_t)__ldg(A.hpre + u) > x + 1 ? (uint32_t)__ldg(A.hpre + u) - 1 : x;
                     const int64_t r1 = A.rp[x + 1];
                     int64_t lo = A.rp[x], hi = r1;
-                    while (lo < hi) {  // first neighbour of x ranked below x
+                    while (lo < hi) {  // first neighbour of x ranked below both x and the prefix
                         const int64_t mid = (lo + hi) >> 1;
-                        if ((uint32_t)__ldg(A.col + mid) <= x) lo = mid + 1; else hi = mid;
+                        if ((uint32_t)__ldg(A.col + mid) <= from) lo = mid + 1; else hi = mid;
                     }
                     const int64_t first = lo;
                     hi = r1;

@@ -45,6 +45,7 @@ struct LevelArgs {
     const int32_t* col;
     const uint32_t* cnt_arc;
     const uint32_t* arc_lo;  // first pulled entry of each arc's segment (dense-prefix skip), or NULL
+    const int32_t* hpre;     // dense prefix per vertex when arc_lo is set
     const uint64_t* seg;  // [levels][n]
     uint64_t* seg_out;    // row d
     uint32_t* hub_arena;
