@@ -7,16 +7,18 @@
 //   above u. Level segments are hub-sorted, so rule 1 keeps a prefix, found
 //   by binary search. The pull of the arc also skips the entries whose hub
 //   lies below u's dense prefix (every rank id up to it is a hub of
-//   L_<d(u), so those entries would be dropped unread by the membership
-//   test of step 2), found by a second binary search. Per vertex the sum is the pulled-entry count (the
-//   paper's cost function); active vertices are bucketed by it so that the
-//   most expensive ones start first.
+//   L_<d(u), so the membership test of step 2 would drop those entries),
+//   found by a second binary search. Per vertex the sum is the
+//   pulled-entry count (the paper's cost function); active vertices are
+//   bucketed by it so that the most expensive ones start first.
 //
 // k_level  (one CTA per vertex, persistent CTAs taking vertices in bucket
-//   order from a work counter)
+//   order from a work counter, or one CTA per vertex when granular)
 //   1. The label map of u: which hubs x are in L_<d(u), and at which
 //      distance. Cumulative bitmaps B_j = {x : d_u(x) <= j}, j = 1..d-1,
-//      when they fit on chip; otherwise an open-addressing hash x -> d_u(x).
+//      when they fit on chip; otherwise a binary search in u's level
+//      segments, with per-level bitmaps over the highest-ranked ids cached
+//      on chip; or (on request) an open-addressing hash x -> d_u(x).
 //   2. Pull: the arcs of u are staged in chunks, their pulled-entry counts
 //      prefix-summed, and the flattened entries split evenly over the
 //      warps. An entry (h, d-1, c) whose hub h is already in L_<d(u) is
@@ -24,22 +26,27 @@
 //      so rule 2 would prune it (Label Elimination at no cost). The others
 //      are merged per hub in an on-chip hash (count += c mod 2^64; the
 //      overflow flag takes the entry's flag and the carry: Label Merging).
-//   3. Landmark filter (Section "Landmark-Based Filtering"), when the build
-//      has landmark distances: a candidate h with sd(u,l) + sd(l,h) < d for
-//      a landmark l is pruned at once, one with |sd(u,l) - sd(l,h)| >= d
-//      survives at once; the others are compacted and go on.
-//      Prune (rule 2) for every remaining candidate h. A common hub x of
-//      L_<d(u) and L_<d(h) with d_u(x) + d_h(x) < d exists iff some
-//      x in L_k(h), 1 <= k <= d-2, has d_u(x) <= d-1-k (the case k = 0,
-//      x = h, was handled in step 2; entries of h at distance d-1 cannot
-//      help because d_u(x) >= 1 for x != u). Groups of lanes take
+//   3a. d = 3: rule 2 asks for a common neighbour of u and h ranked above
+//      h; the rows of u's higher-ranked neighbours are walked once and the
+//      candidates met there are marked.
+//   3. Otherwise: landmark filter (Section "Landmark-Based Filtering"),
+//      when the build has landmark distances: a candidate h with
+//      sd(u,l) + sd(l,h) < d for a landmark l is pruned at once, one with
+//      |sd(u,l) - sd(l,h)| >= d survives at once; the others are compacted
+//      and go on. Prune (rule 2) for every remaining candidate h. A common
+//      hub x of L_<d(u) and L_<d(h) with d_u(x) + d_h(x) < d exists iff
+//      some x in L_k(h), 1 <= k <= d-2, has d_u(x) <= d-1-k (the case
+//      k = 0, x = h, was handled in step 2; entries of h at distance d-1
+//      cannot help because d_u(x) >= 1 for x != u). Groups of lanes take
 //      candidates from a shared counter and scan these segments in level
 //      order with early exit: 8 lanes level by level when u has many
 //      candidates; 16 or 32 lanes over G levels' descriptors read at once,
 //      scanned as one list, when it has few (deep levels of high-diameter
 //      graphs), so that their lanes stay busy.
-//   4. Survivors are sorted by hub (bitonic, on chip) and appended to the
-//      label arena as L_d(u); the arena slot comes from one atomic add.
+//   4. Survivors are put in hub order (the rank of a hub is a popcount over
+//      a bitmap of the survivors, or a bitonic sort when that bitmap does
+//      not fit) and appended to the label arena as L_d(u); the arena slot
+//      comes from one atomic add.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
