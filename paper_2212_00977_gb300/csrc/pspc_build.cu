@@ -9,7 +9,8 @@
 // Vertices are relabelled so that id = rank (0 = highest). Level d of every
 // vertex is one hub-sorted segment of a label arena: a hub word (bits 0-23
 // hub, bit 31 overflow flag) and a uint64 count; the distance is the level.
-// The per-level kernels live in pspc_level.cu.
+// The per-level kernels live in pspc_level.cu, the landmark BFS in
+// pspc_landmark.cu, and the 1-shell reduction in pspc_shell.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>

@@ -1,12 +1,14 @@
 // SPC(s,t) queries on the hub-label index: Eq. (1)-(2) of the paper
 // (Section "2-Hop Labeling for Shortest Path Counting"), evaluated as a
-// warp-cooperative merge-join of the two hub-sorted labels; queries are
-// independent (Section "Reduction by Equivalence Relation", parallel query
-// evaluation), so one warp answers one pair at a time.
+// merge-join of the two hub-sorted labels; queries are independent
+// (Section "Reduction by Equivalence Relation", parallel query evaluation).
 //
-// Per pair: each lane holds one hub of a 32-entry chunk of L(s) and looks
-// it up in the current 32-entry chunk of L(t) with a 5-step shuffle binary
-// search; the chunk whose last hub is smaller advances. A match h gives
+// Kernels: k_query<G> (G lanes per pair, 32-bit hub words in registers,
+// binary search by shuffles), k_query_chunked<CH> (a warp per pair, chunks
+// of CH entries of both labels staged in shared memory, binary search per
+// entry; the side whose last hub is smaller advances), k_query_by_source
+// (pairs sorted by source; L(s) hashed on chip once per run of pairs with
+// that source, each warp streams L(t)). In each, a match h gives
 // dist_s(h) + dist_t(h); counts (and their 128-bit product) are read only
 // for matches that reach the lane's running minimum. The warp then keeps
 // the global minimum and adds the products of the hubs that reach it,
