@@ -1,8 +1,8 @@
 """Autotuner for the SPC library's tuning knobs.
 
-Picks, by timing on the device, the query variant (lanes per pair or
-staged chunk size, ``pspc_set_query_group``) and the build's on-chip table
-sizes and label-map kind (``pspc_opts``). Results never depend on these
+Picks, by timing on the device, the query variant (lanes per pair, staged
+chunk size or by-source, ``pspc_set_query_group``) and the build's on-chip
+table sizes, label-map kind and landmark count (``pspc_opts``). Results never depend on these
 choices; only speed does. Choices are cached per workload class (size and
 density buckets) for the life of the process.
 """
@@ -12,6 +12,7 @@ import math
 
 QUERY_VARIANTS = (1, 16, 32, 64, 128, 256)  # 1 = by source (pspc.PSPC_QUERY_BY_SOURCE)
 BUILD_VARIANTS = tuple(dict(cand_capacity=c, map_kind=m) for c in (2048, 4096, 8192) for m in (0, 2, 3))
+LANDMARK_VARIANTS = (-1, 16, 32, 64)  # second stage: landmark count on top of the best tables
 
 _cache: dict = {}
 
@@ -60,21 +61,30 @@ def tune_query(ix, pairs_dev, reps: int = 3, variants=QUERY_VARIANTS) -> int:
     return _cache[key]
 
 
-def tune_build(build, n: int, arcs: int, reps: int = 1, variants=BUILD_VARIANTS) -> dict:
-    """``build(**opts)`` builds and returns an Index; time each variant on
-    it and return the fastest options (the probe indexes are freed)."""
+def _fastest(build, variants, reps):
+    timing = {}
+    for i, opts in enumerate(variants):
+        def once(o=opts):
+            build(**o).free()
+
+        try:
+            timing[i] = _elapsed_ms(once, reps)
+        except RuntimeError:
+            continue  # a variant the device cannot run (e.g. shared memory)
+    return dict(variants[min(timing, key=timing.get)])
+
+
+def tune_build(build, n: int, arcs: int, reps: int = 1, variants=BUILD_VARIANTS,
+               landmarks=LANDMARK_VARIANTS) -> dict:
+    """``build(**opts)`` builds and returns an Index; time each table
+    variant on it, then the landmark counts on top of the fastest, and
+    return the fastest options (the probe indexes are freed)."""
     key = ("build",) + workload_class(n, arcs)
     if key not in _cache:
-        timing = {}
-        for i, opts in enumerate(variants):
-            def once(o=opts):
-                build(**o).free()
-
-            try:
-                timing[i] = _elapsed_ms(once, reps)
-            except RuntimeError:
-                continue  # a variant the device cannot run (e.g. shared memory)
-        _cache[key] = dict(variants[min(timing, key=timing.get)])
+        best = _fastest(build, variants, reps)
+        if landmarks:
+            best = _fastest(build, tuple(dict(best, landmarks=k) for k in landmarks), reps)
+        _cache[key] = best
     return dict(_cache[key])
 
 
