@@ -2,9 +2,9 @@
 
 Picks, by timing on the device, the query variant (lanes per pair, staged
 chunk size or by-source, ``pspc_set_query_group``) and the build's on-chip
-table sizes, label-map kind and landmark count (``pspc_opts``). Results never depend on these
-choices; only speed does. Choices are cached per workload class (size and
-density buckets) for the life of the process.
+table sizes, label-map kind and landmark count (``pspc_opts``). Results
+never depend on these choices; only speed does. Choices are cached per
+workload class (size and density buckets) for the life of the process.
 """
 from __future__ import annotations
 
