@@ -107,6 +107,14 @@ typedef struct {
                                 hub_column and landmarks are not available
                                 on such an index (PSPC_E_INVAL). pspc_build
                                 only */
+    int32_t paradigm;        /* 0 = pull (Algorithm PULL, the default);
+                                1 = push (Algorithm PUSH): each level, every
+                                vertex first sends its entries to the
+                                buckets of its neighbours in device memory,
+                                then each vertex merges, prunes and appends
+                                from its bucket. Same index; the buckets
+                                hold a level's pulled entries (12 bytes
+                                each), PSPC_E_NOMEM when they do not fit */
 } pspc_opts;
 
 /* Per-level counters of the last build (level d = distance d). */

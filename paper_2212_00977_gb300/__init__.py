@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("cand_capacity", ctypes.c_int32), ("label_capacity", ctypes.c_int32),
                 ("arena_entries", ctypes.c_int64), ("max_levels", ctypes.c_int32),
                 ("verbose", ctypes.c_int32), ("map_kind", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-                ("granular", ctypes.c_int32), ("landmarks", ctypes.c_int32), ("reduce_shell", ctypes.c_int32)]
+                ("granular", ctypes.c_int32), ("landmarks", ctypes.c_int32), ("reduce_shell", ctypes.c_int32),
+                ("paradigm", ctypes.c_int32)]
 
 
 class GraphDesc(ctypes.Structure):
@@ -164,10 +165,11 @@ class Index:
     @classmethod
     def build(cls, n: int, row_ptr, col, rank, *, stream=None, cand_capacity=0, label_capacity=0,
               arena_entries=0, max_levels=0, verbose=False, map_kind=0, max_ctas=0,
-              granular=False, landmarks=0, reduce_shell=False) -> "Index":
+              granular=False, landmarks=0, reduce_shell=False, paradigm=0) -> "Index":
         """pspc_build over a symmetric CSR (rows strictly ascending) and a
         rank permutation (0 = highest). ``reduce_shell`` builds on the
-        2-core and answers peeled tree vertices through their roots."""
+        2-core and answers peeled tree vertices through their roots;
+        ``paradigm=1`` builds each level by push instead of pull."""
         lib = load()
         _check_dtype(row_ptr, np.int64, "row_ptr")
         _check_dtype(col, np.int32, "col")
@@ -175,7 +177,7 @@ class Index:
         g = Csr(int(n), _ptr(row_ptr), _ptr(col))
         o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
                  int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)), int(landmarks),
-                 int(bool(reduce_shell)))
+                 int(bool(reduce_shell)), int(paradigm))
         h = _P()
         rc = lib.pspc_build(ctypes.byref(g), _ptr(rank), ctypes.byref(o), ctypes.byref(h),
                             _stream_handle(stream))

@@ -510,6 +510,11 @@ struct Builder {
     int32_t* hpre = nullptr;       // dense prefix per vertex
     bool skip_prefix = false;      // the current level uses arc_lo
     bool prefix_pays = true;       // the last level that skipped saved enough to go on
+    int64_t* push_off = nullptr;   // push paradigm: bucket offset per arc [arcs+1]
+    uint32_t* push_hub = nullptr;  // push paradigm: the buckets (hub words, counts)
+    uint64_t* push_cnt = nullptr;
+    int64_t push_cap = 0;
+    bool push_level = false;       // the current level runs from the buckets
     int32_t* arc_src = nullptr;
     int32_t* comp_base = nullptr;  // batches: first rank-space id of each vertex's graph
     int64_t max_comp = 0;          // largest graph (bits per level bitmap)
@@ -542,6 +547,9 @@ struct Builder {
         dfree(cnt_arc, st);
         dfree(arc_lo, st);
         dfree(hpre, st);
+        dfree(push_off, st);
+        dfree(push_hub, st);
+        dfree(push_cnt, st);
         dfree(arc_src, st);
         dfree(comp_base, st);
         dfree(raw_u, st);
@@ -851,6 +859,9 @@ struct Builder {
         A.cnt_arc = cnt_arc;
         A.arc_lo = skip_prefix ? arc_lo : nullptr;
         A.hpre = skip_prefix ? hpre : nullptr;
+        A.push_hub = push_level ? push_hub : nullptr;
+        A.push_cnt = push_level ? push_cnt : nullptr;
+        A.push_off = push_level ? push_off : nullptr;
         A.seg = seg;
         A.seg_out = seg + (int64_t)d * n;
         A.hub_arena = hub_arena;
@@ -975,6 +986,32 @@ struct Builder {
         return rc;
     }
 
+    // Push paradigm (Algorithm PUSH): bucket offsets from a scan of the
+    // per-arc counts of the cost pass, then every arc copies its entries.
+    int push_entries(int d) {
+        if (!push_off) PSPC_TRY_CUDA(dalloc(&push_off, arcs + 1, st));
+        PSPC_TRY_CUDA(launch_arc_counts(arcs, cnt_arc, push_off, st));
+        int rc = exclusive_scan_i64(push_off, arcs, st, &out.launches);
+        if (rc) return rc;
+        int64_t total = 0;
+        PSPC_TRY_CUDA(cudaMemcpyAsync(&total, push_off + arcs, 8, cudaMemcpyDeviceToHost, st));
+        PSPC_TRY_CUDA(cudaStreamSynchronize(st));
+        if (total > push_cap) {
+            dfree(push_hub, st);
+            dfree(push_cnt, st);
+            push_hub = nullptr;
+            push_cnt = nullptr;
+            push_cap = 0;
+            PSPC_TRY_CUDA(dalloc(&push_hub, total + total / 4 + 1, st));
+            PSPC_TRY_CUDA(dalloc(&push_cnt, total + total / 4 + 1, st));
+            push_cap = total + total / 4 + 1;
+        }
+        PSPC_TRY_CUDA(launch_push_scatter(arcs, col_r, seg + (int64_t)(d - 1) * n, hub_arena, cnt_arena, cnt_arc,
+                                          skip_prefix ? arc_lo : nullptr, push_off, push_hub, push_cnt, st));
+        out.launches += 3;
+        return PSPC_OK;
+    }
+
     int build_levels() {
         PSPC_TRY_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         LevelPlan plan;
@@ -1053,6 +1090,10 @@ struct Builder {
             if ((rc = read_status())) break;
             if (hstt->n_active == 0) break;
             const long long raw_total = (long long)hstt->raw_total;
+            // Push paradigm: the arcs send their entries into per-vertex
+            // buckets before the level kernel merges them.
+            push_level = o.paradigm == 1;
+            if (push_level && (rc = push_entries(d))) break;
             if (skip_prefix)  // on the graphs measured, the share saved only fell after its first level
                 prefix_pays = (double)hstt->prefix_skipped >=
                               kDensePrefixMinGain * (double)(hstt->prefix_skipped + hstt->raw_total);
@@ -1235,7 +1276,7 @@ static void fill_defaults(pspc_opts& o, const pspc_opts* user) {
 
 static bool opts_ok(const pspc_opts& o) {
     return o.map_kind >= 0 && o.map_kind <= 3 && o.max_ctas >= 0 && (o.granular == 0 || o.granular == 1) &&
-           o.landmarks >= -1 && o.landmarks <= 64;
+           o.landmarks >= -1 && o.landmarks <= 64 && (o.paradigm == 0 || o.paradigm == 1);
 }
 
 static bool pow2_in(int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }

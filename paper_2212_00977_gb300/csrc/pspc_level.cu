@@ -686,16 +686,28 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             }
         }
 
-        // 2. pull with the membership filter, merged per hub
-        const int64_t a0 = A.rp[u], a1 = A.rp[u + 1];
+        // 2. pull with the membership filter, merged per hub. In the push
+        // paradigm the entries sent to u lie in one bucket, read as a
+        // single segment.
+        const bool push = A.push_hub != nullptr;
+        const uint32_t* ghub = push ? A.push_hub : A.hub_arena;
+        const unsigned long long* gcnt =
+            push ? (const unsigned long long*)A.push_cnt : (const unsigned long long*)A.cnt_arena;
+        const int64_t a0 = push ? 0 : A.rp[u], a1 = push ? 1 : A.rp[u + 1];
         for (int64_t ca = a0; ca < a1; ca += kArcChunk) {
             const int nc = (int)((a1 - ca) < kArcChunk ? (a1 - ca) : kArcChunk);
             if (tid < nc) {
-                const uint32_t c = __ldg(A.cnt_arc + ca + tid);
-                pfx[tid] = c;
-                st[tid] = c ? seg_start(__ldg(seg_prev + __ldg(A.col + ca + tid))) +
-                                  (A.arc_lo ? __ldg(A.arc_lo + ca + tid) : 0u)
-                            : 0ull;
+                if (push) {
+                    const int64_t b0 = __ldg(A.push_off + A.rp[u]);
+                    pfx[tid] = __ldg(A.push_off + A.rp[u + 1]) - b0;
+                    st[tid] = (uint64_t)b0;
+                } else {
+                    const uint32_t c = __ldg(A.cnt_arc + ca + tid);
+                    pfx[tid] = c;
+                    st[tid] = c ? seg_start(__ldg(seg_prev + __ldg(A.col + ca + tid))) +
+                                      (A.arc_lo ? __ldg(A.arc_lo + ca + tid) : 0u)
+                                : 0ull;
+                }
             }
             __syncthreads();
             const long long total = block_excl_scan(pfx, nc, s_wsum);
@@ -718,7 +730,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                     if (ok[t]) {
                         while (pfx[j + 1] <= i) ++j;
                         pos[t] = st[j] + (uint64_t)(i - pfx[j]);
-                        hw[t] = __ldg(A.hub_arena + pos[t]);
+                        hw[t] = __ldg(ghub + pos[t]);
                     }
                 }
 #pragma unroll
@@ -730,7 +742,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                 uint64_t cv[kGatherUnroll];
 #pragma unroll
                 for (int t = 0; t < kGatherUnroll; ++t)
-                    if (ok[t]) cv[t] = __ldg((const unsigned long long*)A.cnt_arena + pos[t]);
+                    if (ok[t]) cv[t] = __ldg(gcnt + pos[t]);
 #pragma unroll
                 for (int t = 0; t < kGatherUnroll; ++t)
                     if (ok[t]) cand_insert(ckeys, ccnt, cap_c, limit, hw[t] & kHubMask, cv[t], hw[t] >> 31, &s_nkeys,
@@ -933,6 +945,50 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         if (tid == 0) atomicAdd(&A.stt->unique_total, (unsigned long long)s_nkeys);
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Push paradigm.
+
+__global__ void k_arc_counts(int64_t arcs, const uint32_t* __restrict__ cnt_arc, int64_t* __restrict__ out) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < arcs) out[a] = cnt_arc[a];
+}
+
+// Warp per arc u->v: the entries of L_{d-1}(v) that u receives go to u's
+// bucket in the order they lie in v's segment.
+__global__ void k_push_scatter(int64_t arcs, const int32_t* __restrict__ col, const uint64_t* __restrict__ seg_prev,
+                               const uint32_t* __restrict__ hub_arena, const uint64_t* __restrict__ cnt_arena,
+                               const uint32_t* __restrict__ cnt_arc, const uint32_t* __restrict__ arc_lo,
+                               const int64_t* __restrict__ push_off, uint32_t* __restrict__ push_hub,
+                               uint64_t* __restrict__ push_cnt) {
+    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (a >= arcs) return;
+    const uint32_t c = cnt_arc[a];
+    if (!c) return;
+    const uint64_t src = seg_start(__ldg(seg_prev + col[a])) + (arc_lo ? arc_lo[a] : 0u);
+    const int64_t dst = push_off[a];
+    for (uint32_t i = lane; i < c; i += 32) {
+        push_hub[dst + i] = __ldg(hub_arena + src + i);
+        push_cnt[dst + i] = __ldg((const unsigned long long*)cnt_arena + src + i);
+    }
+}
+
+cudaError_t launch_arc_counts(int64_t arcs, const uint32_t* cnt_arc, int64_t* out, cudaStream_t st) {
+    if (arcs > 0) k_arc_counts<<<(unsigned)((arcs + 255) / 256), 256, 0, st>>>(arcs, cnt_arc, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push_scatter(int64_t arcs, const int32_t* col, const uint64_t* seg_prev,
+                                const uint32_t* hub_arena, const uint64_t* cnt_arena, const uint32_t* cnt_arc,
+                                const uint32_t* arc_lo, const int64_t* push_off, uint32_t* push_hub,
+                                uint64_t* push_cnt, cudaStream_t st) {
+    if (arcs > 0)
+        k_push_scatter<<<(unsigned)((arcs * 32 + 255) / 256), 256, 0, st>>>(arcs, col, seg_prev, hub_arena, cnt_arena,
+                                                                          cnt_arc, arc_lo, push_off, push_hub,
+                                                                          push_cnt);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

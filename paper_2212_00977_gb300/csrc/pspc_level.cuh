@@ -46,6 +46,11 @@ struct LevelArgs {
     const uint32_t* cnt_arc;
     const uint32_t* arc_lo;  // first pulled entry of each arc's segment (dense-prefix skip), or NULL
     const int32_t* hpre;     // dense prefix per vertex when arc_lo is set
+    // Push paradigm: the entries sent to u this level lie in
+    // push_hub/push_cnt[push_off[rp[u]] .. push_off[rp[u+1]]) (NULL: pull).
+    const uint32_t* push_hub;
+    const uint64_t* push_cnt;
+    const int64_t* push_off;
     const uint64_t* seg;  // [levels][n]
     uint64_t* seg_out;    // row d
     uint32_t* hub_arena;
@@ -124,6 +129,15 @@ __host__ __device__ inline size_t level_map_bytes(int kind, int d, uint32_t bm_w
 // distance is above 254 or undefined. Synchronises st once per BFS level.
 int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* comp_base, int k, int stride,
                  uint8_t* ld, cudaStream_t st, int64_t* launches);
+
+// Push paradigm (Algorithm PUSH): every arc u->v sends u the entries of
+// L_{d-1}(v) that the pull would read for it (cnt_arc[a] of them from
+// arc_lo[a], or from 0), into u's bucket at push_off[a]. Warp per arc.
+cudaError_t launch_push_scatter(int64_t arcs, const int32_t* col, const uint64_t* seg_prev,
+                                const uint32_t* hub_arena, const uint64_t* cnt_arena, const uint32_t* cnt_arc,
+                                const uint32_t* arc_lo, const int64_t* push_off, uint32_t* push_hub,
+                                uint64_t* push_cnt, cudaStream_t st);
+cudaError_t launch_arc_counts(int64_t arcs, const uint32_t* cnt_arc, int64_t* out, cudaStream_t st);
 
 // Launchers (pspc_level.cu). Each returns a CUDA error code of the launch.
 cudaError_t launch_arc_src(const int64_t* rp, int64_t n, int32_t* arc_src, cudaStream_t st);

@@ -72,7 +72,8 @@ def test_paper_table(pspc):
 # --- small graphs against the oracle, across table capacities ---
 
 CAPS = [dict(), dict(cand_capacity=1024, label_capacity=1024), dict(map_kind=2, label_capacity=1024),
-        dict(map_kind=3), dict(landmarks=-1), dict(landmarks=64, map_kind=3)]
+        dict(map_kind=3), dict(landmarks=-1), dict(landmarks=64, map_kind=3), dict(paradigm=1),
+        dict(paradigm=1, map_kind=3, cand_capacity=1024)]
 
 
 @pytest.mark.parametrize("seed", range(10))
@@ -409,3 +410,20 @@ def test_level_counters_match_independent_count(pspc, name):
         else:
             assert raw == 0 and ent == 0, d
     ix.free()
+
+
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_ef16", "grid64", "grid32@td"])
+def test_push_paradigm_full_index(pspc, name):
+    """Algorithm PUSH (entries sent to per-vertex buckets, then merged)
+    builds the same index as the pull: the oracle's, bit for bit."""
+    g, rank, pairs_fn = P.workload(name)
+    ref = oracle.OracleIndex(g, rank)
+    ix = gpu_index(pspc, g, rank, paradigm=1)
+    assert_index_equal(ix, ref.export())
+    pairs = pairs_fn(20000)
+    rd, rc, rf, _ = ref.query(pairs)
+    d, c, f = gpu_query(ix, pairs)
+    assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
+    ix.free()
+    with pytest.raises(pspc.PSPCError):
+        gpu_index(pspc, g, rank, paradigm=2)
