@@ -146,3 +146,35 @@ def test_autotuner_keeps_answers(env):
     d, c, f = ix.query(pairs)
     rd, rc, rf, _ = ref.query(pairs.cpu().numpy())
     assert np.array_equal(d.cpu().numpy(), rd) and np.array_equal(c.cpu().numpy(), rc)
+
+
+def test_every_graph_on_six_vertices_in_one_batch(env):
+    """Exhaustive: all 2^15 graphs on 6 vertices, each under a seeded random
+    order, built as one batch; every graph's labels equal the oracle's of
+    that graph alone, and all its ordered pairs answer like the oracle."""
+    torch, pspc = env
+    n = 6
+    pairs6 = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    rng = np.random.default_rng(6)
+    graphs, ranks = [], []
+    for mask in range(1 << len(pairs6)):
+        e = np.array([pairs6[k] for k in range(len(pairs6)) if mask >> k & 1], np.int64).reshape(-1, 2)
+        graphs.append(P.csr_from_edges(n, e))
+        ranks.append(rng.permutation(n).astype(np.int32))
+    ix = pspc.Index.build_batch([(g.n, g.row_ptr, g.col, r) for g, r in zip(graphs, ranks)])
+    try:
+        off, hub, dist, cnt, ovf = ix.export()
+        allp = np.array([(a, b) for a in range(n) for b in range(n)], np.int32)
+        d, c, f = ix.query(np.concatenate([allp + n * i for i in range(len(graphs))]).astype(np.int32))
+        for i, (g, r) in enumerate(zip(graphs, ranks)):
+            ref_ix = oracle.OracleIndex(g, r)
+            ref = ref_ix.export()
+            lo, hi = off[n * i], off[n * (i + 1)]
+            assert np.array_equal(off[n * i:n * (i + 1) + 1] - lo, ref.off), i
+            assert np.array_equal(hub[lo:hi] - n * i, ref.hub), i
+            assert np.array_equal(dist[lo:hi], ref.dist) and np.array_equal(cnt[lo:hi], ref.cnt), i
+            rd, rc, rf, _ = ref_ix.query(allp)
+            s = slice(len(allp) * i, len(allp) * (i + 1))
+            assert np.array_equal(d[s], rd) and np.array_equal(c[s], rc) and np.array_equal(f[s], rf), i
+    finally:
+        ix.free()
