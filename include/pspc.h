@@ -70,8 +70,11 @@ typedef struct {
                                 not fit the device give PSPC_E_INVAL */
     int64_t arena_entries;   /* initial label arena capacity in entries
                                 (default 32 * arcs + 4 * n; grows on demand) */
-    int32_t max_levels;      /* stop with PSPC_E_DIST after this many levels
-                                (default 32767) */
+    int32_t max_levels;      /* distance limit: the build fails with
+                                PSPC_E_DIST when some label entry would
+                                have a distance above it (default and
+                                largest value 32767; distances are stored
+                                in 15 bits) */
     int32_t verbose;         /* 1: per-level line on stderr */
     int32_t map_kind;        /* how a level tests membership in L(u):
                                 0 = automatic (bitmaps when (d-1) bitmaps
@@ -299,14 +302,19 @@ int pspc_set_query_group(pspc_index* ix, int32_t lanes);
  * is a deployment variant of pspc_query, with the same answers.
  *
  * It allocates nothing: no cudaMalloc, cudaFree or pool allocation. Its
- * working memory (the error flag, n+2 per-source bins of 8 bytes, and q
- * pair indices of 4 bytes, each part rounded up to 256 bytes) lives in one
- * static device array of PSPC_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU
- * which loads the library holds until the process exits.
- * pairs, dist, count and overflow (may be NULL) must be device memory of
- * the index's device; host pointers would need staging buffers and are
- * rejected. q must satisfy 256 + round256(8*(n+2)) + 4*q <= 16 MiB
- * (about 4.06M pairs for n = 65,536); larger q gives PSPC_E_INVAL. The
+ * working memory lives in one static device array of
+ * PSPC_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the
+ * library holds until the process exits. Like pspc_query, a call groups its
+ * pairs by source only when q >= 4096 and q >= n/4; such a call needs, in
+ * the array, the error flag (256 bytes), n+2 per-source bins of 8 bytes,
+ * the scan's partial sums (8 bytes per 4096 bins, rounded up), and q pair
+ * indices of 4 bytes, each part rounded up to 256 bytes. A grouped call
+ * that does not fit returns PSPC_E_INVAL: about 4.06M pairs for n = 65,536,
+ * and none for n above about 2.09M (the bins alone fill the array). A call
+ * that does not group uses only the error flag and has no size limit
+ * (q < 2^40). pairs, dist, count and overflow (may be NULL) must be device
+ * memory of the index's device; host pointers would need staging buffers
+ * and are rejected. The call waits for its stream before it returns. The
  * first call on a device looks up the array's device address; make that
  * first call before any stream capture. Every call shares the array and
  * clears what it counts in; calls that overlap on the GPU (on different
@@ -330,6 +338,18 @@ int pspc_query_noalloc(const pspc_index* ix, const int32_t* pairs, int64_t q, ui
  * Errors: PSPC_E_INVAL (NULL index or k), PSPC_E_NOMEM, PSPC_E_CUDA.
  */
 int pspc_landmarks(const pspc_index* ix, int32_t* k, uint8_t* dist);
+
+/*
+ * pspc_inject_alloc_failure -- fault injection for tests of the library's
+ * out-of-memory paths (the paper has no counterpart). After this call the
+ * library's next `after` device allocations succeed and every later one
+ * fails as if the device were out of memory: the call that needed it
+ * returns PSPC_E_NOMEM, releases what it holds, and leaves *out = NULL for
+ * a build. after < 0 removes the limit (the default). Process-wide, for
+ * every device; pspc_query_noalloc allocates nothing and is unaffected.
+ * Returns PSPC_OK.
+ */
+int pspc_inject_alloc_failure(int64_t after);
 
 /* pspc_free -- release an index and all its device memory; NULL is a no-op. */
 void pspc_free(pspc_index* ix);

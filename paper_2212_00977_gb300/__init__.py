@@ -90,6 +90,7 @@ _SIGS = {
     "pspc_hub_column": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "pspc_query_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "pspc_landmarks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), _P]),
+    "pspc_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
     "pspc_free": (None, [_P]),
     "pspc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -112,6 +113,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         if path is None:
             _lib = lib
         return lib
+
+
+def inject_alloc_failure(after: int) -> None:
+    """pspc_inject_alloc_failure: the library's next ``after`` device
+    allocations succeed and later ones fail (PSPC_E_NOMEM); ``after`` < 0
+    removes the limit. For tests of the out-of-memory paths."""
+    load().pspc_inject_alloc_failure(int(after))
 
 
 def strerror(code: int) -> str:

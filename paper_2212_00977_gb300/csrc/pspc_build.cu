@@ -1046,11 +1046,11 @@ struct Builder {
         PSPC_TRY_CUDA(cudaEventCreate(&ek0));
         PSPC_TRY_CUDA(cudaEventCreate(&ek1));
         int levels = 1;
+        // Distances are stored in 15 bits: a level beyond the limit that
+        // adds an entry ends the build with PSPC_E_DIST (one that adds
+        // nothing is the normal end).
+        const int dist_limit = std::min(o.max_levels, kMaxDist);
         for (int d = 1;; ++d) {
-            if (d > o.max_levels || d > kMaxDist) {
-                rc = PSPC_E_DIST;
-                break;
-            }
             if ((rc = ensure_seg_levels(d + 1))) break;
             if ((rc = plan_level(d, plan))) break;
             cudaEventRecord(e0, st);
@@ -1066,6 +1066,10 @@ struct Builder {
                     fprintf(stderr, "pspc level 1: entries %lld active %lld %.3f ms\n", (long long)ls.entries,
                             (long long)ls.active_vertices, ls.ms);
                 if (ls.entries == 0) break;
+                if (d > dist_limit) {
+                    rc = PSPC_E_DIST;
+                    break;
+                }
                 lvl_base.push_back(bump);
                 levels = 2;
                 continue;
@@ -1153,6 +1157,10 @@ struct Builder {
                 fprintf(stderr, "pspc level %d: raw %lld unique %lld entries %lld active %d (off-chip %d) %.3f ms\n",
                         d, raw_total, (long long)hstt->unique_total, added, hstt->n_active, n_off, ms);
             if (added == 0) break;
+            if (d > dist_limit) {
+                rc = PSPC_E_DIST;
+                break;
+            }
             lvl_base.push_back(bump);
             levels = d + 1;
         }

@@ -88,8 +88,13 @@ void dev_free(void* p, cudaStream_t st);
 
 // Exclusive prefix sum of int64 values in place: a[0..n) -> exclusive
 // scan, a[n] = total (a must hold n+1 values). Device memory.
-// *launches (if not NULL) is increased by the kernels launched.
-int exclusive_scan_i64(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches = nullptr);
+// *launches (if not NULL) is increased by the kernels launched. The tile
+// partial sums go to `scratch` when it is given (device memory of at least
+// scan_scratch_entries(n + 1) values), else to memory from the pool.
+int exclusive_scan_i64(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches = nullptr,
+                       int64_t* scratch = nullptr);
+// Partial-sum values the scan of m values needs (0 when one tile holds them).
+int64_t scan_scratch_entries(int64_t m);
 
 }  // namespace pspc
 

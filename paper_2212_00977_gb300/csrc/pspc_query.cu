@@ -484,6 +484,12 @@ static int query_group_for(const Index& ix, bool grouped, int64_t q) {
     return avg >= 128.0 ? 256 : (avg >= 24.0 ? 16 : 8);
 }
 
+// Whether a call groups its pairs by source (both pspc_query and
+// pspc_query_noalloc): when sources repeat enough for L(s) to be reused.
+static bool groups_by_source(const Index& ix, int64_t q) {
+    return q >= 4096 && q >= ix.n / 4 && q < ((int64_t)1 << 31);
+}
+
 // Launches the query kernel chosen for the index (Q.perm is the grouping
 // sort's order, or NULL). Counts the launch on the index.
 static cudaError_t launch_query(Index& ix, const QueryArgs& Q, cudaStream_t st) {
@@ -637,7 +643,7 @@ extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q,
     // Group by source when sources repeat enough for L(s) to be reused.
     int32_t* d_perm = nullptr;
     int64_t* d_bins = nullptr;
-    const bool group = q >= 4096 && q >= ix.n / 4 && q < ((int64_t)1 << 31);
+    const bool group = groups_by_source(ix, q);
     if (e == cudaSuccess && group) {
         const int32_t* pin = dev_in ? pairs : d_pairs;
         e = dev_alloc((void**)&d_perm, (size_t)q * 4, st);
@@ -743,57 +749,22 @@ static cudaError_t noalloc_scratch(int dev, unsigned char** out) {
     return cudaSuccess;
 }
 
-// Exclusive scan of a[0..m) in place, a[m] = total, by one block (1024
-// threads walking the array in tiles with a running carry).
-__global__ void __launch_bounds__(1024) k_scan_one_block(long long* a, int64_t m) {
-    __shared__ long long s_warp[32];
-    __shared__ long long s_carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < m; base += 1024) {
-        const int64_t i = base + tid;
-        const long long v = i < m ? a[i] : 0;
-        long long incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            long long t = s_warp[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long u = __shfl_up_sync(0xFFFFFFFFu, t, o);
-                if (lane >= o) t += u;
-            }
-            s_warp[lane] = t;
-        }
-        __syncthreads();
-        const long long carry = s_carry;
-        if (i < m) a[i] = carry + incl - v + (warp ? s_warp[warp - 1] : 0);
-        __syncthreads();
-        if (tid == 0) s_carry = carry + s_warp[31];
-        __syncthreads();
-    }
-    if (tid == 0) a[m] = s_carry;
-}
-
 }  // namespace pspc
 
 extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, int64_t q, uint16_t* dist,
                                   uint64_t* count, uint8_t* overflow, void* stream) {
-    if (!hc || q < 0) return PSPC_E_INVAL;
+    if (!hc || q < 0 || q >= ((int64_t)1 << 40)) return PSPC_E_INVAL;
     if (q == 0) return PSPC_OK;
     if (!pairs || !dist || !count || hc->ix.core) return PSPC_E_INVAL;
     pspc_index* h = const_cast<pspc_index*>(hc);  // only the launch counter changes
     const Index& ix = h->ix;
-    // Scratch layout: error flag | n+2 source bins | q pair indices.
+    // Scratch layout: error flag | n+2 source bins | scan partials | q pair
+    // indices. Only calls that group by source use more than the flag.
+    const bool group = groups_by_source(ix, q);
     const size_t bins_off = 256;
-    const size_t perm_off = bins_off + (((size_t)(ix.n + 2) * 8 + 255) & ~(size_t)255);
-    if (perm_off + (size_t)q * 4 > kNoallocScratchBytes || q >= ((int64_t)1 << 31)) return PSPC_E_INVAL;
+    const size_t part_off = bins_off + (((size_t)(ix.n + 2) * 8 + 255) & ~(size_t)255);
+    const size_t perm_off = part_off + (((size_t)scan_scratch_entries(ix.n + 2) * 8 + 255) & ~(size_t)255);
+    if (group && perm_off + (size_t)q * 4 > kNoallocScratchBytes) return PSPC_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -807,20 +778,28 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
     if (rc == PSPC_OK) e = noalloc_scratch(ix.device, &scratch);
     if (rc == PSPC_OK && e == cudaSuccess) {
         int* d_err = (int*)scratch;
-        long long* d_bins = (long long*)(scratch + bins_off);
-        int32_t* d_perm = (int32_t*)(scratch + perm_off);
+        int64_t* d_bins = (int64_t*)(scratch + bins_off);
+        int64_t* d_part = (int64_t*)(scratch + part_off);
+        int32_t* d_perm = group ? (int32_t*)(scratch + perm_off) : nullptr;
         // The array keeps the previous call's contents: clear what is counted.
         e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_bins, 0, (size_t)(ix.n + 2) * 8, st);
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && group) e = cudaMemsetAsync(d_bins, 0, (size_t)(ix.n + 2) * 8, st);
+        if (e == cudaSuccess && group) {
             k_pair_hist<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pairs, q, ix.n, (unsigned long long*)d_bins);
-            k_scan_one_block<<<1, 1024, 0, st>>>(d_bins, ix.n + 1);
-            k_pair_scatter<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pairs, q, ix.n, (unsigned long long*)d_bins,
-                                                                       d_perm);
-            __atomic_fetch_add(&h->ix.query_launches, (int64_t)3, __ATOMIC_RELAXED);
+            __atomic_fetch_add(&h->ix.query_launches, (int64_t)2, __ATOMIC_RELAXED);
             e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                int64_t scan_launches = 0;
+                rc = exclusive_scan_i64(d_bins, ix.n + 1, st, &scan_launches, d_part);
+                __atomic_fetch_add(&h->ix.query_launches, scan_launches, __ATOMIC_RELAXED);
+            }
+            if (e == cudaSuccess && rc == PSPC_OK) {
+                k_pair_scatter<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(pairs, q, ix.n,
+                                                                           (unsigned long long*)d_bins, d_perm);
+                e = cudaGetLastError();
+            }
         }
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && rc == PSPC_OK) {
             QueryArgs Q;
             Q.n = ix.n;
             Q.rank = ix.rank;
@@ -840,7 +819,7 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
         int herr = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess && herr) rc = PSPC_E_INVAL;
+        if (e == cudaSuccess && herr && rc == PSPC_OK) rc = PSPC_E_INVAL;
     }
     if (e != cudaSuccess) rc = cuda_status(e);
     if (prev != ix.device) cudaSetDevice(prev);

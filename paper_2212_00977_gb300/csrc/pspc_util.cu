@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -29,7 +30,24 @@ static std::mutex g_pool_mu;
 static cudaMemPool_t g_pools[64];
 static bool g_pool_ok[64];
 
+// Allocation-failure injection (pspc_inject_alloc_failure): the number of
+// library device allocations still allowed to succeed, or -1 (no limit).
+static std::atomic<int64_t> g_alloc_budget{-1};
+
+static bool alloc_allowed() {
+    int64_t b = g_alloc_budget.load(std::memory_order_relaxed);
+    while (b >= 0) {
+        if (b == 0) return false;
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1, std::memory_order_relaxed)) return true;
+    }
+    return true;
+}
+
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+    if (!alloc_allowed()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -117,7 +135,16 @@ __global__ void k_scan_add(int64_t* a, int64_t n, const int64_t* tile_offs) {
     if (i < n) a[i] += tile_offs[i / kScanTile];
 }
 
-static int scan_rec(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches) {
+int64_t scan_scratch_entries(int64_t n) {
+    int64_t total = 0;
+    while (n > kScanTile) {
+        n = (n + kScanTile - 1) / kScanTile;
+        total += n;
+    }
+    return total;
+}
+
+static int scan_rec(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches, int64_t* scratch) {
     if (n <= 0) return PSPC_OK;
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 1) {
@@ -125,28 +152,33 @@ static int scan_rec(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches) {
         if (launches) *launches += 1;
         return cuda_status(cudaGetLastError());
     }
-    int64_t* sums = nullptr;
-    PSPC_TRY_CUDA(dev_alloc((void**)&sums, (size_t)tiles * sizeof(int64_t), st));
+    int64_t* sums = scratch;
+    if (!sums) PSPC_TRY_CUDA(dev_alloc((void**)&sums, (size_t)tiles * sizeof(int64_t), st));
     k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(a, n, sums);
     int rc = cuda_status(cudaGetLastError());
-    if (rc == PSPC_OK) rc = scan_rec(sums, tiles, st, launches);
+    if (rc == PSPC_OK) rc = scan_rec(sums, tiles, st, launches, scratch ? scratch + tiles : nullptr);
     if (rc == PSPC_OK) {
         k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, n, sums);
         rc = cuda_status(cudaGetLastError());
     }
     if (launches) *launches += 2;
-    dev_free(sums, st);
+    if (!scratch) dev_free(sums, st);
     return rc;
 }
 
-int exclusive_scan_i64(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches) {
+int exclusive_scan_i64(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches, int64_t* scratch) {
     PSPC_TRY_CUDA(cudaMemsetAsync(a + n, 0, sizeof(int64_t), st));
-    return scan_rec(a, n + 1, st, launches);
+    return scan_rec(a, n + 1, st, launches, scratch);
 }
 
 }  // namespace pspc
 
 using namespace pspc;
+
+extern "C" int pspc_inject_alloc_failure(int64_t after) {
+    g_alloc_budget.store(after < 0 ? -1 : after, std::memory_order_relaxed);
+    return PSPC_OK;
+}
 
 extern "C" const char* pspc_strerror(int code) {
     switch (code) {

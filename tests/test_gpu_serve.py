@@ -1,5 +1,5 @@
 """Serving: continuously batched queries and overlapping builds give every
-request exactly the answer it gets alone."""
+request exactly the answer the oracle gives, and the answer it gets alone."""
 from __future__ import annotations
 
 import threading
@@ -8,6 +8,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 import pspc_inputs as P
 from tests import _graphs as G
 
@@ -70,8 +71,14 @@ def test_results_same_alone_and_in_the_mix(env):
             bad.wait(60)
         good.wait(60)
         alone = {"A": A, "B": B, "C": srv.indexes["C"][0], "D": srv.indexes["D"][0]}
+        # the oracle's index of every graph (C and D were built by the
+        # server while the queries ran)
+        orc = {"A": oracle.OracleIndex(ga, ra), "B": oracle.OracleIndex(gb, rb),
+               "C": oracle.OracleIndex(gc, G.random_rank(gc.n, 2)), "D": oracle.OracleIndex(gd, G.degree_rank(gd))}
         for name, pairs, r in reqs:
             d, c, f = r.wait(60)
+            od, oc, of, _ = orc[name].query(pairs)
+            assert np.array_equal(d, od) and np.array_equal(c, oc) and np.array_equal(f, of)
             rd, rc, rf = alone[name].query(pairs)
             assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
         assert srv.batches < len(reqs)  # requests were batched

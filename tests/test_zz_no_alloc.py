@@ -2,13 +2,14 @@
 cannot allocate device memory while they query (their device memory is owned
 by another allocator, or their serving loop must never enter the driver's
 allocator). It must give exactly the answers of pspc_query, call after call,
-through the C ABI. Collected last on purpose: a failure here leaves every
-other test already run."""
+through the C ABI, and the oracle's. Collected last on purpose: a failure
+here leaves every other test already run."""
 from __future__ import annotations
 
 import numpy as np
 import pytest
 
+import oracle
 import pspc_inputs as P
 
 pytestmark = pytest.mark.gpu
@@ -34,24 +35,36 @@ def _noalloc(lib, ix, pairs_d, torch, fill):
     return rc, d.cpu().numpy(), c.cpu().numpy(), f.cpu().numpy()
 
 
-@pytest.mark.parametrize("name", ["rmat12_ef16", "grid32"])
-def test_noalloc_matches_query_on_two_calls_in_a_row(env, name):
+# (workload, pairs): 300,000 pairs group by source (by-source or staged
+# kernels fed by the call's own permutation); 1,000 pairs do not group, and
+# the plain kernels run in caller order (k_query<16> on BA 2000, the staged
+# k_query_chunked<256> on the larger labels of R-MAT 12 and grid 32).
+@pytest.mark.parametrize("name,q", [("rmat12_ef16", 300000), ("grid32", 300000), ("rmat12_ef16", 1000),
+                                    ("grid32", 1000), ("ba2000", 1000), ("ba2000", 5000)])
+def test_noalloc_matches_query_on_two_calls_in_a_row(env, name, q):
     torch, pspc, lib = env
     g, rank, pairs_fn = P.workload(name)
     dev = torch.device("cuda:0")
     ix = pspc.Index.build(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
                           torch.from_numpy(rank).to(dev))
-    pairs = pairs_fn(300000)
+    pairs = pairs_fn(q)
     pairs[:7] = [[0, 0], [1, 1], [0, g.n - 1], [g.n - 1, 0], [5, 9], [9, 5], [3, 3]]
     pairs_d = torch.from_numpy(pairs).to(dev)
     rd, rc, rf = ix.query(pairs_d)
     ref = (rd.cpu().numpy(), rc.cpu().numpy(), rf.cpu().numpy())
+    od, oc, of, _ = oracle.OracleIndex(g, rank).query(pairs)
+    assert np.array_equal(ref[0], od) and np.array_equal(ref[1], oc) and np.array_equal(ref[2], of)
     # two calls in a row, each starting from different garbage in the outputs;
-    # the shared scratch keeps the first call's contents for the second
-    for fill in (0, 7):
-        status, d, c, f = _noalloc(lib, ix, pairs_d, torch, fill)
-        assert status == pspc.PSPC_OK
-        assert np.array_equal(d, ref[0]) and np.array_equal(c, ref[1]) and np.array_equal(f, ref[2])
+    # the shared scratch keeps the first call's contents for the second.
+    # Every library allocation fails meanwhile: the calls must not need one.
+    pspc.inject_alloc_failure(0)
+    try:
+        for fill in (0, 7):
+            status, d, c, f = _noalloc(lib, ix, pairs_d, torch, fill)
+            assert status == pspc.PSPC_OK
+            assert np.array_equal(d, ref[0]) and np.array_equal(c, ref[1]) and np.array_equal(f, ref[2])
+    finally:
+        pspc.inject_alloc_failure(-1)
     ix.free()
 
 
@@ -67,7 +80,9 @@ def test_noalloc_rejects_what_it_cannot_serve_without_allocating(env):
     f = np.empty(1000, np.uint8)
     assert lib.pspc_query_noalloc(ix._h, pairs.ctypes.data, 1000, d.ctypes.data, c.ctypes.data, f.ctypes.data,
                                   None) == pspc.PSPC_E_INVAL
-    # more pairs than the static working array holds
+    # a grouped call (q >= 4096 and q >= n/4) with more pairs than the
+    # static working array holds: flag, bins (the n+2 bins fit one scan tile
+    # here, so there are no scan partials), pair indices
     limit = (16 << 20) - 256 - ((8 * (g.n + 2) + 255) // 256) * 256
     q_big = limit // 4 + 1
     big = torch.zeros((q_big, 2), dtype=torch.int32, device=dev)
