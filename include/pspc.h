@@ -95,7 +95,7 @@ typedef struct {
                                 "Landmark-Based Filtering"): the K highest-
                                 ranked vertices of every graph are
                                 landmarks, and their exact BFS distances to
-                                every vertex (one byte each) let the prune
+                                every vertex (two bytes each) let the prune
                                 step drop a candidate h of u at level d at
                                 once when sd(u,l) + sd(l,h) < d for some
                                 landmark l. 0 = default (K = 32), -1 = off,
@@ -331,13 +331,12 @@ int pspc_query_noalloc(const pspc_index* ix, const int32_t* pairs, int64_t q, ui
  * filter (Section "Landmark-Based Filtering"; the landmarks of a graph are
  * its k highest-ranked vertices, k = pspc_opts.landmarks).
  * k:    host int32 out; the landmarks per graph (0 when the filter was off).
- * dist: NULL, or host uint8[n][k] out by caller vertex id: dist[v*k + j] =
- *       sd(v, j-th highest-ranked vertex of v's graph), or 255 when that
- *       distance is above 254, the two are not connected, or v's graph has
- *       no j-th vertex.
+ * dist: NULL, or host uint16[n][k] out by caller vertex id: dist[v*k + j] =
+ *       sd(v, j-th highest-ranked vertex of v's graph), or 0xFFFF when the
+ *       two are not connected or v's graph has no j-th vertex.
  * Errors: PSPC_E_INVAL (NULL index or k), PSPC_E_NOMEM, PSPC_E_CUDA.
  */
-int pspc_landmarks(const pspc_index* ix, int32_t* k, uint8_t* dist);
+int pspc_landmarks(const pspc_index* ix, int32_t* k, uint16_t* dist);
 
 /*
  * pspc_inject_alloc_failure -- fault injection for tests of the library's

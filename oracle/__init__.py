@@ -74,6 +74,10 @@ def _load():
         lib.orc_bfs_count.argtypes = [I64, P, P, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32]
         lib.orc_hub_column.restype = ctypes.c_int
         lib.orc_hub_column.argtypes = [I64, P, P, P, ctypes.c_int32, P, P, P]
+        lib.orc_spc_pairs.restype = ctypes.c_int
+        lib.orc_spc_pairs.argtypes = [I64, P, P, P, I64, P, P, P]
+        lib.orc_check_columns.restype = I64
+        lib.orc_check_columns.argtypes = [I64, P, P, P, P, I64, P, P, P, P, P, P, P, P, I64]
         _lib = lib
         return lib
 
@@ -208,3 +212,48 @@ def hub_column(g, rank: np.ndarray, w: int):
     if lib.orc_hub_column(n, _ptr(rp), _ptr(col), _ptr(rk), int(w), _ptr(d), _ptr(c), _ptr(f)):
         raise MemoryError("hub column allocation failed")
     return d, c, f
+
+
+def spc_pairs(g, pairs: np.ndarray):
+    """SPC of int32[q,2] pairs by breadth-first path counting, one search
+    per distinct source, sources in parallel on the host cores: (dist uint16
+    with 0xFFFF = unreachable, cnt uint64, ovf uint8, threads used)."""
+    lib = _load()
+    n = int(g.n)
+    p = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    if p.size and (p.min() < 0 or p.max() >= n):
+        raise ValueError("pair vertex out of range")
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    q = len(p)
+    d = np.empty(q, np.uint16)
+    c = np.empty(q, np.uint64)
+    f = np.empty(q, np.uint8)
+    th = lib.orc_spc_pairs(n, _ptr(rp), _ptr(col), _ptr(p), q, _ptr(d), _ptr(c), _ptr(f))
+    if th < 0:
+        raise MemoryError("spc_pairs allocation failed")
+    return d, c, f, int(th)
+
+
+def check_columns(g, rank: np.ndarray, hubs, off, hub, dist, cnt, ovf, max_bad: int = 16):
+    """Compare an exported index (caller ids, labels in hub-rank order) with
+    the definition, column by column for the given hubs, in parallel on the
+    host cores. Returns (mismatching (hub, vertex) pairs, entries the
+    definition gives for these hubs, list of the first bad (hub, vertex))."""
+    lib = _load()
+    n = int(g.n)
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    rk = np.ascontiguousarray(rank, dtype=np.int32)
+    hs = np.ascontiguousarray(hubs, dtype=np.int32)
+    arrs = [np.ascontiguousarray(a) for a in (off, hub, dist, cnt, ovf)]
+    assert [a.dtype for a in arrs] == [np.int64, np.int32, np.uint16, np.uint64, np.uint8]
+    bw = np.zeros(max_bad, np.int32)
+    bv = np.zeros(max_bad, np.int32)
+    ent = ctypes.c_int64()
+    bad = lib.orc_check_columns(n, _ptr(rp), _ptr(col), _ptr(rk), _ptr(hs), len(hs), *[_ptr(a) for a in arrs],
+                                ctypes.byref(ent), _ptr(bw), _ptr(bv), max_bad)
+    if bad < 0:
+        raise MemoryError("check_columns allocation failed")
+    k = min(int(bad), max_bad)
+    return int(bad), int(ent.value), list(zip(bw[:k].tolist(), bv[:k].tolist()))

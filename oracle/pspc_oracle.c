@@ -370,3 +370,161 @@ int orc_hub_column(int64_t n, const int64_t* row_ptr, const int32_t* col, const 
     free(d_true); free(d_tr); free(c_true); free(f_true); free(queue);
     return 0;
 }
+
+/*
+ * SPC of many pairs straight from the definition: one breadth-first path
+ * count per distinct source, answering every pair with that source.
+ * Sources run in parallel with OpenMP (each thread with its own search
+ * arrays). Same conventions as orc_query: SPC(s,s) = (0,1), unreachable =
+ * (0xFFFF, 0, 0). Returns the threads used, or -1 on allocation failure.
+ */
+int orc_spc_pairs(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* pairs, int64_t q,
+                  uint16_t* out_dist, uint64_t* out_cnt, uint8_t* out_ovf) {
+    int64_t* first = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t)); /* pairs of source s: bucket s */
+    int64_t* by_src = (int64_t*)malloc((size_t)(q ? q : 1) * sizeof(int64_t));
+    int32_t* srcs = (int32_t*)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    if (!first || !by_src || !srcs) {
+        free(first); free(by_src); free(srcs);
+        return -1;
+    }
+    for (int64_t k = 0; k < q; ++k) first[pairs[2 * k] + 1]++;
+    int64_t ns = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (first[v + 1]) srcs[ns++] = (int32_t)v;
+        first[v + 1] += first[v];
+    }
+    {
+        int64_t* fill = (int64_t*)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+        if (!fill) {
+            free(first); free(by_src); free(srcs);
+            return -1;
+        }
+        memcpy(fill, first, (size_t)n * sizeof(int64_t));
+        for (int64_t k = 0; k < q; ++k) by_src[fill[pairs[2 * k]]++] = k;
+        free(fill);
+    }
+    int threads = 1, failed = 0;
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+#ifdef _OPENMP
+#pragma omp single
+        threads = omp_get_num_threads();
+#endif
+        int32_t* d = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+        uint64_t* c = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+        uint8_t* f = (uint8_t*)malloc((size_t)n);
+        int32_t* queue = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+        if (!d || !c || !f || !queue) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            failed = 1;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t i = 0; i < ns; ++i) {
+            if (!d || !c || !f || !queue) continue;
+            const int32_t s = srcs[i];
+            orc_bfs_count(n, row_ptr, col, s, d, c, f, queue, NULL, 0);
+            for (int64_t j = first[s]; j < first[s + 1]; ++j) {
+                const int64_t k = by_src[j];
+                const int32_t t = pairs[2 * k + 1];
+                if (d[t] < 0) {
+                    out_dist[k] = ORC_UNREACHED;
+                    out_cnt[k] = 0;
+                    out_ovf[k] = 0;
+                } else {
+                    out_dist[k] = (uint16_t)d[t];
+                    out_cnt[k] = c[t];
+                    out_ovf[k] = f[t];
+                }
+            }
+        }
+        free(d); free(c); free(f); free(queue);
+    }
+    free(first); free(by_src); free(srcs);
+    return failed ? -1 : threads;
+}
+
+/*
+ * Whole-index check from the definition, parallel over hubs: for every hub
+ * w of hubs[0..nh) (caller ids) the column of w is computed as in
+ * orc_hub_column (a true and a restricted breadth-first search) and
+ * compared with the exported index (off, hub, dist, cnt, ovf: per vertex
+ * its entries in hub-rank order, hubs as caller ids), where the entry of w
+ * in L(v) is found by binary search on rank. An entry that the definition
+ * gives and the index lacks or holds with another distance, count or flag
+ * is a mismatch, and so is an index entry for w where the definition gives
+ * none. *entries receives the number of entries the definition gives for
+ * these hubs (for all n hubs, it must equal the index size: then no label
+ * holds an entry of any other hub). Returns the number of mismatching
+ * (hub, vertex) pairs (the first `max_bad` of them in bad_w/bad_v), or -1
+ * on allocation failure.
+ */
+int64_t orc_check_columns(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* rank,
+                          const int32_t* hubs, int64_t nh, const int64_t* off, const int32_t* hub,
+                          const uint16_t* dist, const uint64_t* cnt, const uint8_t* ovf, int64_t* entries,
+                          int32_t* bad_w, int32_t* bad_v, int64_t max_bad) {
+    int64_t nbad = 0, ent = 0;
+    int failed = 0;
+#ifdef _OPENMP
+#pragma omp parallel reduction(+ : ent)
+#endif
+    {
+        int32_t* dt = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+        int32_t* dr = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+        uint64_t* ct = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+        uint64_t* cr = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+        uint8_t* ft = (uint8_t*)malloc((size_t)n);
+        uint8_t* fr = (uint8_t*)malloc((size_t)n);
+        int32_t* queue = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+        const int ok = dt && dr && ct && cr && ft && fr && queue;
+        if (!ok) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            failed = 1;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t i = 0; i < nh; ++i) {
+            if (!ok) continue;
+            const int32_t w = hubs[i];
+            const int32_t rw = rank[w];
+            orc_bfs_count(n, row_ptr, col, w, dt, ct, ft, queue, NULL, 0);
+            orc_bfs_count(n, row_ptr, col, w, dr, cr, fr, queue, rank, rw);
+            for (int64_t v = 0; v < n; ++v) {
+                const int expect = dr[v] >= 0 && dr[v] == dt[v];
+                /* entry of w in L(v): labels are sorted by hub rank */
+                int64_t lo = off[v], hi = off[v + 1];
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (rank[hub[mid]] < rw) lo = mid + 1; else hi = mid;
+                }
+                const int have = lo < off[v + 1] && hub[lo] == w;
+                int bad = expect != have;
+                if (!bad && expect)
+                    bad = dist[lo] != (uint16_t)dr[v] || cnt[lo] != cr[v] || ovf[lo] != fr[v];
+                ent += expect;
+                if (bad) {
+                    int64_t k;
+#ifdef _OPENMP
+#pragma omp atomic capture
+#endif
+                    k = nbad++;
+                    if (k < max_bad) {
+                        bad_w[k] = w;
+                        bad_v[k] = (int32_t)v;
+                    }
+                }
+            }
+        }
+        free(dt); free(dr); free(ct); free(cr); free(ft); free(fr); free(queue);
+    }
+    *entries = ent;
+    return failed ? -1 : nbad;
+}

@@ -274,15 +274,15 @@ class Index:
         return {f: getattr(s, f) for f, _ in Stats._fields_}
 
     def landmarks(self) -> np.ndarray:
-        """pspc_landmarks: uint8 [n, k] distances from each vertex to the k
-        highest-ranked vertices of its graph (255 = above 254 or none);
+        """pspc_landmarks: uint16 [n, k] distances from each vertex to the k
+        highest-ranked vertices of its graph (0xFFFF = unreached or none);
         k = 0 when the build ran without the landmark filter."""
         lib = load()
         k = ctypes.c_int32()
         rc = lib.pspc_landmarks(self._h, ctypes.byref(k), None)
         if rc != PSPC_OK:
             raise PSPCError(rc, "pspc_landmarks")
-        out = np.empty((self.n, k.value), dtype=np.uint8)
+        out = np.empty((self.n, k.value), dtype=np.uint16)
         if k.value:
             rc = lib.pspc_landmarks(self._h, ctypes.byref(k), _ptr(out))
             if rc != PSPC_OK:

@@ -328,11 +328,36 @@ struct FinArgs {
     size_t gscratch_stride;  // keys per CTA
 };
 
+// Exclusive scan of one value per thread of a kFinThreads block into pre[];
+// returns the total. Ends with a barrier.
+__device__ int fin_block_scan(uint32_t v, int* pre, int* wtot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int incl = (int)v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kFinThreads / 32; ++w) {
+        before += w < warp ? wtot[w] : 0;
+        total += wtot[w];
+    }
+    pre[tid] = before + incl - (int)v;
+    __syncthreads();
+    return total;
+}
+
 template <bool kOffChip>
 __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinArgs F) {
     extern __shared__ __align__(16) unsigned long long s_keys[];
     __shared__ int s_item;
     __shared__ unsigned long long s_ovf;
+    __shared__ int s_pre[kFinThreads];
+    __shared__ int s_wtot[kFinThreads / 32];
+    __shared__ uint64_t s_st[kFinThreads];
     unsigned long long* keys = kOffChip ? F.gscratch + (size_t)blockIdx.x * F.gscratch_stride : s_keys;
     const int tid = threadIdx.x;
     if (tid == 0) s_ovf = 0;
@@ -353,14 +378,27 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinArgs F) {
             __syncthreads();
             continue;
         }
+        // Level descriptors are read kFinThreads at a time (one per thread)
+        // and prefix-summed, so that a vertex of a high-diameter graph does
+        // not walk its levels one by one.
         int64_t f0 = 0;
-        for (int l = 0; l < F.levels; ++l) {
-            const uint64_t s = F.seg[(int64_t)l * F.n + u];
-            const uint32_t len = seg_len(s);
-            const uint64_t st = seg_start(s);
-            for (uint32_t i = tid; i < len; i += kFinThreads)
-                keys[f0 + i] = ((unsigned long long)(__ldg(F.hub_arena + st + i) & kHubMask) << 40) | (st + i);
-            f0 += len;
+        for (int l0 = 0; l0 < F.levels; l0 += kFinThreads) {
+            const int l = l0 + tid;
+            const uint64_t s = l < F.levels ? F.seg[(int64_t)l * F.n + u] : 0ull;
+            const int total = fin_block_scan(seg_len(s), s_pre, s_wtot);
+            s_st[tid] = seg_start(s);
+            __syncthreads();
+            for (int i = tid; i < total; i += kFinThreads) {
+                int lo = 0, hi = kFinThreads - 1;  // last level j of the chunk with s_pre[j] <= i
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= i) lo = mid; else hi = mid - 1;
+                }
+                const uint64_t pos = s_st[lo] + (uint64_t)(i - s_pre[lo]);
+                keys[f0 + i] = ((unsigned long long)(__ldg(F.hub_arena + pos) & kHubMask) << 40) | pos;
+            }
+            f0 += total;
+            __syncthreads();
         }
         const uint32_t P = pow2_ceil((uint64_t)T);
         for (uint32_t i = (uint32_t)T + tid; i < P; i += kFinThreads) keys[i] = ~0ull;
@@ -826,7 +864,9 @@ struct Builder {
 
     int ensure_seg_levels(int need) {
         if (need <= seg_levels_cap) return PSPC_OK;
-        int cap = std::max(need, seg_levels_cap ? seg_levels_cap * 2 : 16);
+        // rows for levels 0 .. kMaxDist + 1 at most (the level after the
+        // storage limit is run to learn whether it is empty)
+        int cap = std::max(need, std::min(seg_levels_cap ? seg_levels_cap * 2 : 16, kMaxDist + 2));
         uint64_t* s2 = nullptr;
         PSPC_TRY_CUDA(dalloc(&s2, (size_t)cap * n, st));
         if (seg)
@@ -969,7 +1009,7 @@ struct Builder {
     // the index.
     int landmarks() {
         out.lmk_k = o.landmarks;
-        out.lmk_stride = (o.landmarks + 15) / 16 * 16;
+        out.lmk_stride = (2 * o.landmarks + 15) / 16 * 16;
         PSPC_TRY_CUDA(dalloc(&out.lmk, n * out.lmk_stride, st));
         cudaEvent_t a, b;
         PSPC_TRY_CUDA(cudaEventCreate(&a));

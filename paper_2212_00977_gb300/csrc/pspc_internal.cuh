@@ -58,9 +58,9 @@ struct Index {
     int64_t query_launches = 0;  // kernels launched by pspc_query on this index
     int32_t query_group = 0;  // lanes per query pair; 0 = chosen from label sizes
     int32_t graphs = 1;       // graphs in the batch the index was built from
-    uint8_t* lmk = nullptr;   // [n][lmk_stride] landmark distances (rank ids), or NULL
+    uint8_t* lmk = nullptr;   // [n][lmk_stride] bytes: uint16 landmark distances (rank ids), or NULL
     int32_t lmk_k = 0;        // landmarks per graph
-    int32_t lmk_stride = 0;   // bytes per row (lmk_k rounded up to 16)
+    int32_t lmk_stride = 0;   // bytes per row (2 * lmk_k rounded up to 16)
     float lmk_ms = 0.f;       // device time of the landmark BFS
     // 1-shell reduction: when `core` is set, the labels are those of the
     // 2-core, held by `core` (an index over core ids), and every vertex of G

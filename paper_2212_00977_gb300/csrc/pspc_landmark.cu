@@ -19,7 +19,12 @@ namespace pspc {
 constexpr int kLmkGroup = 8;         // lanes per vertex in a BFS level
 constexpr int kLmkThreads = 256;
 constexpr int kLmkLevelsPerCheck = 4;  // BFS levels launched between host checks
-constexpr int kLmkMaxDist = 254;     // 255 marks "above 254 or undefined"
+constexpr int kLmkMaxDist = 65534;   // 0xFFFF marks "unreached" (or no such landmark)
+
+// Row v of the distance table: `stride` bytes holding k uint16 distances.
+__device__ __forceinline__ uint16_t* lmk_row(uint8_t* ld, int64_t v, int stride) {
+    return (uint16_t*)(ld + v * stride);
+}
 
 __global__ void k_lmk_init(int64_t n, int k, int stride, const int32_t* __restrict__ comp_base,
                            uint64_t* __restrict__ visited, uint64_t* __restrict__ frontier, uint8_t* __restrict__ ld) {
@@ -31,7 +36,7 @@ __global__ void k_lmk_init(int64_t n, int k, int stride, const int32_t* __restri
     const bool is_lmk = j < k;
     visited[v] = is_lmk ? (1ull << j) : 0ull;
     frontier[v] = visited[v];
-    if (is_lmk) ld[v * stride + j] = 0;
+    if (is_lmk) lmk_row(ld, v, stride)[j] = 0;
 }
 
 // One BFS level for all landmarks: kLmkGroup lanes per vertex OR the
@@ -60,12 +65,12 @@ __global__ void __launch_bounds__(kLmkThreads)
         }
     }
     for (int j = gl; j < 64; j += kLmkGroup)
-        if ((fresh >> j) & 1ull) ld[v * stride + j] = (uint8_t)level;
+        if ((fresh >> j) & 1ull) lmk_row(ld, v, stride)[j] = (uint16_t)level;
 }
 
 int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* comp_base, int k, int stride,
                  uint8_t* ld, cudaStream_t st, int64_t* launches) {
-    if (k < 1 || k > 64 || stride % 16 || stride < k) return PSPC_E_INVAL;
+    if (k < 1 || k > 64 || stride % 16 || stride < 2 * k) return PSPC_E_INVAL;
     void* mem = nullptr;
     const size_t masks = (size_t)n * 8;
     cudaError_t e = dev_alloc(&mem, 3 * masks + 256, st);

@@ -433,10 +433,27 @@ __device__ void prune_candidates(const Map& mp, const uint64_t* __restrict__ seg
 
 // Rule 2 level by level: G lanes per candidate scan L_1(h), then L_2(h), ...
 // (one descriptor read per level), kProbeUnroll loads in flight per lane.
+// A witness x in L_k(h) has sd(h,x) = k, and sd(u,h) >= d-2, so d_u(x) is
+// d-2-k or d-1-k: x lies in one of u's two level segments thr-1, thr
+// (thr = d-1-k; level 0 is u itself, never in L(h)). When those two are
+// much shorter than L_k(h), the group scans them instead and looks each
+// entry up in L_k(h) (hub-sorted) by binary search. useg holds u's level
+// descriptors for levels 0 .. kUSideLevels-1 (NULL: always scan L_k(h)).
+constexpr int kUSideLevels = 16;
+
+__device__ __forceinline__ bool seg_contains(const uint32_t* xs, uint32_t len, uint32_t x) {
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((__ldg(xs + mid) & kHubMask) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo < len && (__ldg(xs + lo) & kHubMask) == x;
+}
+
 template <int G, class Map>
 __device__ void prune_by_level(const Map& mp, const uint64_t* __restrict__ seg,
                                const uint32_t* __restrict__ hub_arena, int64_t n, int d, uint32_t* list,
-                               const uint32_t* ckeys, int M, int* next) {
+                               const uint32_t* ckeys, int M, int* next, const uint64_t* useg) {
     auto tile = cg::tiled_partition<G>(cg::this_thread_block());
     const int gl = tile.thread_rank();
     for (;;) {
@@ -453,6 +470,28 @@ __device__ void prune_by_level(const Map& mp, const uint64_t* __restrict__ seg,
             const uint32_t len = seg_len(s);
             const uint32_t* xs = hub_arena + seg_start(s);
             const int thr = d - 1 - k;
+            if (useg && thr < kUSideLevels && len > 0) {
+                const uint64_t ua = thr >= 2 ? useg[thr - 1] : 0ull, ub = useg[thr];
+                const uint32_t la = seg_len(ua), lb = seg_len(ub);
+                const uint32_t steps = 32 - __clz(len);  // binary-search steps in L_k(h)
+                if ((uint64_t)(la + lb) * steps < len) {
+                    const uint32_t* xa = hub_arena + seg_start(ua);
+                    const uint32_t* xb = hub_arena + seg_start(ub);
+                    for (uint32_t b = 0; b < la + lb && !pruned; b += G * kProbeUnroll) {
+                        bool hit = false;
+#pragma unroll
+                        for (int t = 0; t < kProbeUnroll; ++t) {
+                            const uint32_t i = b + t * G + gl;
+                            if (i < la + lb) {
+                                const uint32_t x = __ldg(i < la ? xa + i : xb + (i - la)) & kHubMask;
+                                hit |= seg_contains(xs, len, x);
+                            }
+                        }
+                        pruned = tile.any(hit);
+                    }
+                    continue;
+                }
+            }
             for (uint32_t b = 0; b < len && !pruned; b += G * kProbeUnroll) {
                 uint32_t x[kProbeUnroll];
 #pragma unroll
@@ -478,8 +517,8 @@ __device__ void prune_by_level(const Map& mp, const uint64_t* __restrict__ seg,
 template <class Map>
 __device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, const uint32_t* hub_arena, int64_t n,
                                           int d, uint32_t* list, const uint32_t* ckeys, int M, int to_scan,
-                                          int* next) {
-    if (to_scan >= 64) prune_by_level<8>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
+                                          int* next, const uint64_t* useg) {
+    if (to_scan >= 64) prune_by_level<8>(mp, seg, hub_arena, n, d, list, ckeys, M, next, useg);
     else if (to_scan >= 16) prune_candidates<16>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
     else prune_candidates<32>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
 }
@@ -489,9 +528,9 @@ __device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, co
 // l bounds sd(u,h) from both sides: sd(u,h) <= sd(u,l) + sd(l,h), and
 // sd(u,h) >= |sd(u,l) - sd(l,h)|. An upper bound below d prunes h at once;
 // a lower bound of at least d proves that h survives (it keeps its list
-// entry, marked kProvenBit, and skips the label scan). Distances are bytes
-// (255 = unknown): the sum is taken with saturation and compared with
-// min(d, 255), so an unknown or saturated sum never prunes, and a byte 255
+// entry, marked kProvenBit, and skips the label scan). Distances are uint16
+// (0xFFFF = unknown): the sum is taken with saturation and compared with d
+// (at most 32767), so an unknown or saturated sum never prunes, and 0xFFFF
 // on either side gives no lower bound. The candidates not pruned are
 // compacted to list[0..kept) in the same order (in rounds of one candidate
 // per thread: every read of a round precedes its writes, and no write
@@ -500,7 +539,7 @@ __device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, co
 __device__ int landmark_filter(const LevelArgs& A, const uint32_t* s_lmk, int d, uint32_t* list,
                                const uint32_t* ckeys, int M, int* s_wcnt, int* s_kept, int* n_proven) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t dd = (uint32_t)(d < 255 ? d : 255) * 0x01010101u;
+    const uint32_t dd = (uint32_t)d * 0x00010001u;  // d <= 32767 in both halfwords
     const int words = A.lmk_stride / 16;
     int kept = 0, proven = 0;
     for (int base = 0; base < M; base += kLevelThreads) {
@@ -511,17 +550,19 @@ __device__ int landmark_filter(const LevelArgs& A, const uint32_t* s_lmk, int d,
             slot = list[c];
             const uint4* row = (const uint4*)(A.lmk + (size_t)(ckeys[slot] & kHubMask) * A.lmk_stride);
             uint32_t hit = 0, far = 0;
+            // two uint16 distances per word; 0xFFFF (undefined) saturates
+            // the sum and is masked out of the difference test
 #pragma unroll
-            for (int w = 0; w < 4; ++w)
+            for (int w = 0; w < 8; ++w)
                 if (w < words) {
                     const uint4 b4 = __ldg(row + w);
                     const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const uint32_t a = s_lmk[4 * w + q], b = bw[q];
-                        hit |= __vcmpltu4(__vaddus4(a, b), dd);
-                        const uint32_t known = ~(__vcmpeq4(a, 0xFFFFFFFFu) | __vcmpeq4(b, 0xFFFFFFFFu));
-                        far |= __vcmpgeu4(__vabsdiffu4(a, b), dd) & known;
+                        hit |= __vcmpltu2(__vaddus2(a, b), dd);
+                        const uint32_t known = ~(__vcmpeq2(a, 0xFFFFFFFFu) | __vcmpeq2(b, 0xFFFFFFFFu));
+                        far |= __vcmpgeu2(__vabsdiffu2(a, b), dd) & known;
                     }
                 }
             keep = hit == 0u;
@@ -573,7 +614,8 @@ template <int kMap, bool kOffChip>
 __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_item, s_nkeys, s_abort, s_m, s_next, s_nsurv, s_kept;
-    __shared__ uint32_t s_lmk[16];  // u's landmark distances (bytes)
+    __shared__ uint32_t s_lmk[32];  // u's landmark distances (uint16 pairs)
+    __shared__ uint64_t s_useg[kUSideLevels];  // u's level descriptors for the rule-2 scan
     __shared__ int s_wcnt[kLevelThreads / 32];
     __shared__ unsigned long long s_base;
     __shared__ long long s_wsum[kLevelThreads / 32];
@@ -859,10 +901,17 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         }
         if (d >= 3 && !marked && M_scan > n_proven) {
             const int ns = M_scan - n_proven;
-            if constexpr (kMap == kMapBitmap) prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next);
+            // u's level descriptors, for scanning u's side when it is shorter
+            // (not with bitmaps: their probes cost one on-chip read)
+            const bool useg_on = kMap != kMapBitmap && d - 2 < kUSideLevels;
+            if (useg_on && tid < d - 1) s_useg[tid] = __ldg(A.seg + (int64_t)tid * n + u);
+            __syncthreads();
+            const uint64_t* useg = useg_on ? s_useg : nullptr;
+            if constexpr (kMap == kMapBitmap)
+                prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg);
             else if constexpr (kMap == kMapHash)
-                prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next);
-            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next);
+                prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg);
+            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg);
             __syncthreads();
         }
         M = M_scan;  // list[0..M) now holds every candidate that can survive

@@ -70,8 +70,8 @@ struct LevelArgs {
     int granular;              // 1: CTA b handles item b only (grid = n_items); 0: persistent
     uint8_t* gscratch;    // per-CTA table memory when the tables are off chip
     size_t gscratch_stride;
-    const uint8_t* lmk;   // [n][lmk_stride] landmark distances, or NULL (no filter)
-    int lmk_stride;       // multiple of 16, <= 64
+    const uint8_t* lmk;   // [n][lmk_stride] bytes of uint16 landmark distances, or NULL (no filter)
+    int lmk_stride;       // bytes per row: a multiple of 16, <= 128
 };
 
 // Table layout (on chip, or in per-CTA device scratch). The map region also
@@ -125,8 +125,9 @@ __host__ __device__ inline size_t level_map_bytes(int kind, int d, uint32_t bm_w
 // Landmark labelling (pspc_landmark.cu): exact BFS distances from the k
 // highest-ranked vertices of every graph (rank-space ids comp_base[v] + j,
 // or j when comp_base is NULL), all k searches at once with one 64-bit mask
-// of reached landmarks per vertex. ld is [n][stride] bytes, 255 where the
-// distance is above 254 or undefined. Synchronises st once per BFS level.
+// of reached landmarks per vertex. ld is [n][stride] bytes, k uint16
+// distances per row, 0xFFFF where the distance is undefined (unreached, or
+// no such landmark). Synchronises st every few BFS levels.
 int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* comp_base, int k, int stride,
                  uint8_t* ld, cudaStream_t st, int64_t* launches);
 

@@ -245,7 +245,7 @@ extern "C" int pspc_stats(const pspc_index* h, pspc_stats_t* s) {
     return PSPC_OK;
 }
 
-extern "C" int pspc_landmarks(const pspc_index* h, int32_t* k, uint8_t* dist) {
+extern "C" int pspc_landmarks(const pspc_index* h, int32_t* k, uint16_t* dist) {
     if (!h || !k || h->ix.core) return PSPC_E_INVAL;
     const Index& ix = h->ix;
     *k = ix.lmk ? ix.lmk_k : 0;
@@ -268,7 +268,7 @@ extern "C" int pspc_landmarks(const pspc_index* h, int32_t* k, uint8_t* dist) {
     if (!rc && e == cudaSuccess) e = cudaMemcpy(rank.data(), ix.rank, (size_t)ix.n * 4, cudaMemcpyDeviceToHost);
     if (!rc && e != cudaSuccess) rc = cuda_status(e);
     if (!rc)
-        for (int64_t v = 0; v < ix.n; ++v) memcpy(dist + (size_t)v * K, rows.data() + (size_t)rank[v] * S, K);
+        for (int64_t v = 0; v < ix.n; ++v) memcpy(dist + (size_t)v * K, rows.data() + (size_t)rank[v] * S, 2 * K);
     cudaSetDevice(prev);
     return rc;
 }

@@ -1,7 +1,7 @@
 """Landmark filter of pruning rule 2 (Section "Landmark-Based Filtering").
 
 The landmark distances the build computes are checked against breadth-first
-search in the oracle (exact, capped at 254), and the index built with the
+search in the oracle (exact, 16 bits), and the index built with the
 filter, at several landmark counts and with it off, is checked against the
 oracle bit for bit: the filter may only change speed."""
 from __future__ import annotations
@@ -33,13 +33,13 @@ def _order(rank):
 
 
 def expected_landmarks(g, rank, k):
-    """dist[v, j] = sd(v, j-th highest-ranked vertex) from oracle BFS; 255
-    above 254, when unreachable, or when the graph has no j-th vertex."""
-    out = np.full((g.n, k), 255, np.uint8)
+    """dist[v, j] = sd(v, j-th highest-ranked vertex) from oracle BFS;
+    0xFFFF when unreachable or when the graph has no j-th vertex."""
+    out = np.full((g.n, k), 0xFFFF, np.uint16)
     order = _order(rank)
     for j in range(min(k, g.n)):
         d, _, _ = oracle.bfs_count(g, int(order[j]))
-        ok = (d >= 0) & (d <= 254)
+        ok = d >= 0
         out[ok, j] = d[ok]
     return out
 
