@@ -13,7 +13,11 @@ Three independent implementations of the same result:
   labeler in rank order (HP-SPC, Section "Order Property"), the Eq. (1)-(2)
   merge-join query, breadth-first path counting, and the per-hub column
   check straight from the definition, all in C with uint64 counts wrapping
-  mod 2^64 and an overflow flag set iff the exact value is >= 2^64.
+  mod 2^64 and an overflow flag set iff the exact value is >= 2^64. For the
+  full-size workloads the same definitions run in parallel on the host
+  cores: columns of many hubs (:func:`hub_columns`), a whole exported index
+  checked column by column (:func:`check_columns`), and query answers by
+  one breadth-first count per source (:func:`spc_pairs`).
 
 ``build_lib()`` compiles the C file with gcc into ``oracle/_oracle_build``.
 """
@@ -74,6 +78,8 @@ def _load():
         lib.orc_bfs_count.argtypes = [I64, P, P, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32]
         lib.orc_hub_column.restype = ctypes.c_int
         lib.orc_hub_column.argtypes = [I64, P, P, P, ctypes.c_int32, P, P, P]
+        lib.orc_hub_columns.restype = ctypes.c_int
+        lib.orc_hub_columns.argtypes = [I64, P, P, P, P, I64, P, P, P]
         lib.orc_spc_pairs.restype = ctypes.c_int
         lib.orc_spc_pairs.argtypes = [I64, P, P, P, I64, P, P, P]
         lib.orc_check_columns.restype = I64
@@ -236,10 +242,13 @@ def spc_pairs(g, pairs: np.ndarray):
 
 
 def check_columns(g, rank: np.ndarray, hubs, off, hub, dist, cnt, ovf, max_bad: int = 16):
-    """Compare an exported index (caller ids, labels in hub-rank order) with
-    the definition, column by column for the given hubs, in parallel on the
-    host cores. Returns (mismatching (hub, vertex) pairs, entries the
-    definition gives for these hubs, list of the first bad (hub, vertex))."""
+    """Compare an exported index (caller ids, labels in strictly increasing
+    hub rank) with the definition, column by column for the given hubs, in
+    parallel on the host cores: every entry the definition gives must be in
+    the index with its distance, count and flag. Returns (mismatching (hub,
+    vertex) pairs, entries the definition gives for these hubs, list of the
+    first bad (hub, vertex)); with all hubs, an entry total equal to the
+    index size means the index holds nothing else."""
     lib = _load()
     n = int(g.n)
     rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
@@ -257,3 +266,21 @@ def check_columns(g, rank: np.ndarray, hubs, off, hub, dist, cnt, ovf, max_bad: 
         raise MemoryError("check_columns allocation failed")
     k = min(int(bad), max_bad)
     return int(bad), int(ent.value), list(zip(bw[:k].tolist(), bv[:k].tolist()))
+
+
+def hub_columns(g, rank: np.ndarray, hubs):
+    """hub_column for many hubs, in parallel on the host cores: arrays
+    [len(hubs), n] of (dist uint16 with 0xFFFF where there is no entry,
+    cnt uint64, ovf uint8)."""
+    lib = _load()
+    n = int(g.n)
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    rk = np.ascontiguousarray(rank, dtype=np.int32)
+    hs = np.ascontiguousarray(hubs, dtype=np.int32)
+    d = np.empty((len(hs), n), np.uint16)
+    c = np.empty((len(hs), n), np.uint64)
+    f = np.empty((len(hs), n), np.uint8)
+    if lib.orc_hub_columns(n, _ptr(rp), _ptr(col), _ptr(rk), _ptr(hs), len(hs), _ptr(d), _ptr(c), _ptr(f)) < 0:
+        raise MemoryError("hub_columns allocation failed")
+    return d, c, f

@@ -79,18 +79,3 @@ def spc_all(n: int, edges):
     """All-pairs (dist, count) tables from breadth-first counting."""
     adj = adjacency(n, edges)
     return [bfs_paths(adj, s) for s in range(n)]
-
-
-def query_labels(L, s: int, t: int, rank):
-    """Eq. (1)-(2) evaluated on exact-count labels (s != t)."""
-    a = {h: (d, c) for h, d, c in L[s]}
-    best = None
-    total = 0
-    for h, d, c in L[t]:
-        if h in a:
-            dd = a[h][0] + d
-            if best is None or dd < best:
-                best, total = dd, a[h][1] * c
-            elif dd == best:
-                total += a[h][1] * c
-    return best, total

@@ -454,15 +454,15 @@ int orc_spc_pairs(int64_t n, const int64_t* row_ptr, const int32_t* col, const i
  * w of hubs[0..nh) (caller ids) the column of w is computed as in
  * orc_hub_column (a true and a restricted breadth-first search) and
  * compared with the exported index (off, hub, dist, cnt, ovf: per vertex
- * its entries in hub-rank order, hubs as caller ids), where the entry of w
- * in L(v) is found by binary search on rank. An entry that the definition
- * gives and the index lacks or holds with another distance, count or flag
- * is a mismatch, and so is an index entry for w where the definition gives
- * none. *entries receives the number of entries the definition gives for
- * these hubs (for all n hubs, it must equal the index size: then no label
- * holds an entry of any other hub). Returns the number of mismatching
- * (hub, vertex) pairs (the first `max_bad` of them in bad_w/bad_v), or -1
- * on allocation failure.
+ * its entries in strictly increasing hub rank, hubs as caller ids), where
+ * the entry of w in L(v) is found by binary search on rank. An entry that
+ * the definition gives and the index lacks, or holds with another
+ * distance, count or flag, is a mismatch. *entries receives the number of
+ * entries the definition gives for these hubs: for all n hubs it must
+ * equal the index size, and then, every expected entry having been found
+ * at its own position, the index holds nothing else. Returns the number of
+ * mismatching (hub, vertex) pairs (the first `max_bad` of them in
+ * bad_w/bad_v), or -1 on allocation failure.
  */
 int64_t orc_check_columns(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* rank,
                           const int32_t* hubs, int64_t nh, const int64_t* off, const int32_t* hub,
@@ -499,6 +499,7 @@ int64_t orc_check_columns(int64_t n, const int64_t* row_ptr, const int32_t* col,
             orc_bfs_count(n, row_ptr, col, w, dr, cr, fr, queue, rank, rw);
             for (int64_t v = 0; v < n; ++v) {
                 const int expect = dr[v] >= 0 && dr[v] == dt[v];
+                if (!expect) continue;
                 /* entry of w in L(v): labels are sorted by hub rank */
                 int64_t lo = off[v], hi = off[v + 1];
                 while (lo < hi) {
@@ -506,10 +507,8 @@ int64_t orc_check_columns(int64_t n, const int64_t* row_ptr, const int32_t* col,
                     if (rank[hub[mid]] < rw) lo = mid + 1; else hi = mid;
                 }
                 const int have = lo < off[v + 1] && hub[lo] == w;
-                int bad = expect != have;
-                if (!bad && expect)
-                    bad = dist[lo] != (uint16_t)dr[v] || cnt[lo] != cr[v] || ovf[lo] != fr[v];
-                ent += expect;
+                const int bad = !have || dist[lo] != (uint16_t)dr[v] || cnt[lo] != cr[v] || ovf[lo] != fr[v];
+                ent += 1;
                 if (bad) {
                     int64_t k;
 #ifdef _OPENMP
@@ -527,4 +526,36 @@ int64_t orc_check_columns(int64_t n, const int64_t* row_ptr, const int32_t* col,
     }
     *entries = ent;
     return failed ? -1 : nbad;
+}
+
+/*
+ * Columns of many hubs at once, as orc_hub_column computes one, in
+ * parallel over the hubs: row i of out_dist/out_cnt/out_ovf (n values each)
+ * is the column of hubs[i]. Returns the threads used, or -1 on allocation
+ * failure.
+ */
+int orc_hub_columns(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* rank,
+                    const int32_t* hubs, int64_t nh, uint16_t* out_dist, uint64_t* out_cnt, uint8_t* out_ovf) {
+    int threads = 1, failed = 0;
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+#ifdef _OPENMP
+#pragma omp single
+        threads = omp_get_num_threads();
+#endif
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t i = 0; i < nh; ++i) {
+            if (orc_hub_column(n, row_ptr, col, rank, hubs[i], out_dist + i * n, out_cnt + i * n, out_ovf + i * n)) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                failed = 1;
+            }
+        }
+    }
+    return failed ? -1 : threads;
 }

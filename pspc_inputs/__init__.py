@@ -31,7 +31,6 @@ __all__ = [
     "ba_batch",
     "elimination_order",
     "hybrid_rank",
-    "read_edge_list",
 ]
 
 
@@ -265,29 +264,6 @@ def hybrid_rank(g: Graph, delta: int | None = 5) -> np.ndarray:
     rank = np.empty(g.n, dtype=np.int32)
     rank[order] = np.arange(g.n, dtype=np.int32)
     return rank
-
-
-def read_edge_list(path: str, name: str = "") -> tuple[Graph, np.ndarray]:
-    """An edge list file as used by SNAP and KONECT: one edge per line, two
-    vertex ids separated by whitespace or a comma; lines starting with '#'
-    or '%' and extra columns (weights, times) are ignored. Ids are relabelled
-    compactly in increasing order; the graph is symmetrised without loops
-    or duplicates (as the paper does with its directed datasets). Returns
-    (graph, original ids of the vertices 0..n-1)."""
-    src, dst = [], []
-    with open(path) as fh:
-        for line in fh:
-            line = line.strip()
-            if not line or line[0] in "#%":
-                continue
-            parts = line.replace(",", " ").split()
-            if len(parts) < 2:
-                continue
-            src.append(int(parts[0]))
-            dst.append(int(parts[1]))
-    ids = np.unique(np.array(src + dst, dtype=np.int64))
-    e = np.stack([np.searchsorted(ids, src), np.searchsorted(ids, dst)], axis=1) if src else np.zeros((0, 2), np.int64)
-    return csr_from_edges(len(ids), e, name or path), ids
 
 
 def query_pairs(n: int, q: int, seed: int) -> np.ndarray:

@@ -59,12 +59,3 @@ def test_oracle_counts_match_networkx(seed):
         paths = list(nx.all_shortest_paths(G, s, t))
         assert dd == len(paths[0]) - 1
         assert cc == len(paths)
-
-
-def test_read_edge_list(tmp_path):
-    p = tmp_path / "g.txt"
-    p.write_text("# comment\n% konect header\n10 20\n20,30 1.5\n30 10\n10 10\n20 10\n\n40 50 7 8\n")
-    g, ids = P.read_edge_list(str(p))
-    assert ids.tolist() == [10, 20, 30, 40, 50]
-    assert g.n == 5 and g.m == 4  # 10-20, 20-30, 30-10, 40-50; the loop and the repeat are dropped
-    assert sorted(map(tuple, g.edges().tolist())) == [(0, 1), (0, 2), (1, 2), (3, 4)]

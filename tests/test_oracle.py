@@ -299,3 +299,109 @@ def test_ba_batch_is_seeded_and_pool_independent():
     assert len(a) == 6
     for x, y in zip(a, b):
         assert x[0] == y[0] and all(np.array_equal(u, v) for u, v in zip(x[1:], y[1:]))
+
+
+# --- the parallel pair counter and the whole-index column checker ---
+
+def test_spc_pairs_vs_exact_bfs_and_closed_forms():
+    """oracle.spc_pairs (breadth-first counting per source, in parallel)
+    equals exact big-integer counting on random graphs, every pair, and the
+    textbook counts, overflow flags included."""
+    for seed in range(4):
+        rng = np.random.default_rng(seed)
+        n = int(rng.integers(10, 50))
+        g = G.gnp(n, 0.12, 70 + seed)
+        pairs = np.array(list(itertools.product(range(n), range(n))), np.int32)
+        allp = brute.spc_all(n, g.edges())
+        perm = rng.permutation(len(pairs))
+        qd, qc, qf, th = oracle.spc_pairs(g, pairs[perm])
+        assert th >= 1
+        for k, (s, t) in enumerate(pairs[perm]):
+            d, c = allp[s]
+            if t in d:
+                assert (qd[k], qc[k], qf[k]) == (d[t], c[t] % M64, int(c[t] >= M64))
+            else:
+                assert (qd[k], qc[k], qf[k]) == (oracle.UNREACHED, 0, 0)
+    for g, s, t, sd, cnt in G.closed_forms():
+        qd, qc, qf, _ = oracle.spc_pairs(g, np.array([[s, t], [t, s], [s, s]], np.int32))
+        assert qd.tolist() == [sd, sd, 0]
+        assert qc.tolist() == [cnt % M64, cnt % M64, 1]
+        assert qf.tolist() == [int(cnt >= M64)] * 2 + [0]
+
+
+def _brute_export(n, edges, rank):
+    """Exact labels from the definition, in the export layout (counts mod
+    2^64 and flags)."""
+    L = brute.labels(n, edges, rank)
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in L])
+    flat = [e for x in L for e in x]
+    hub = np.array([h for h, _, _ in flat], np.int32)
+    dist = np.array([d for _, d, _ in flat], np.uint16)
+    cnt = np.array([c % M64 for _, _, c in flat], np.uint64)
+    ovf = np.array([int(c >= M64) for _, _, c in flat], np.uint8)
+    return off, hub, dist, cnt, ovf
+
+
+def test_check_columns_accepts_the_definition_and_finds_planted_mistakes():
+    """oracle.check_columns passes the exact labels of the definition on
+    graphs with several components and overflowing counts, and reports a
+    mistake planted anywhere: a changed distance, count or flag, a dropped
+    entry, an extra entry (caught by the entry total) and a swapped hub."""
+    cases = [(G.gnp(40, 0.1, 3), 5), (G.grid(36), 7), (G.diamond_chain(65), 2)]
+    for g, seed in cases:
+        rank = G.random_rank(g.n, seed)
+        exp = _brute_export(g.n, g.edges(), rank)
+        bad, ent, _ = oracle.check_columns(g, rank, np.arange(g.n), *exp)
+        assert bad == 0 and ent == int(exp[0][-1])
+        rng = np.random.default_rng(seed)
+        E = int(exp[0][-1])
+        i = int(rng.integers(0, E))
+        for field, delta in ((2, 1), (3, 1), (4, 1)):
+            m = [a.copy() for a in exp]
+            m[field][i] = m[field][i] + delta if field != 4 else 1 - m[field][i]
+            bad, _, first = oracle.check_columns(g, rank, np.arange(g.n), *m)
+            assert bad >= 1 and first[0][0] == exp[1][i]
+        # drop the entry i: its vertex loses one entry
+        v = int(np.searchsorted(exp[0], i, side="right") - 1)
+        keep = np.ones(E, bool)
+        keep[i] = False
+        off2 = exp[0].copy()
+        off2[v + 1:] -= 1
+        dropped = (off2, exp[1][keep], exp[2][keep], exp[3][keep], exp[4][keep])
+        bad, ent, _ = oracle.check_columns(g, rank, np.arange(g.n), *dropped)
+        assert bad == 1 and ent == E
+        # a hub swapped for another vertex's id: its own entry goes missing
+        m = [a.copy() for a in exp]
+        j = int(np.flatnonzero(m[2] > 0)[0])  # not a self entry
+        m[1][j] = int(np.argmax(rank))  # the lowest-ranked vertex is nobody's hub but its own
+        bad, _, _ = oracle.check_columns(g, rank, np.arange(g.n), *m)
+        assert bad >= 1
+        # an extra entry: every expected entry is still found, and the total
+        # the definition gives is below the index size
+        v = int(np.argmin(rank))  # the highest-ranked vertex has only its self entry
+        x = int(np.argsort(rank)[1])
+        off3 = exp[0].copy()
+        off3[v + 1:] += 1
+        pos = int(exp[0][v]) + 1  # after v's self entry: ranks stay increasing
+        extra = (off3, np.insert(exp[1], pos, x), np.insert(exp[2], pos, 1), np.insert(exp[3], pos, 1),
+                 np.insert(exp[4], pos, 0))
+        bad, ent, _ = oracle.check_columns(g, rank, np.arange(g.n), *extra)
+        assert bad == 0 and ent == E and int(off3[-1]) == E + 1
+
+
+def test_hub_columns_equal_the_definition():
+    """oracle.hub_columns (many hub columns, in parallel) equals the exact
+    labels of the definition, hub by hub, overflow flags included."""
+    for g, seed in ((G.gnp(50, 0.08, 9), 1), (G.grid(36), 4)):
+        rank = G.random_rank(g.n, seed)
+        L = brute.labels(g.n, g.edges(), rank)
+        hubs = np.random.default_rng(seed).permutation(g.n)[:40]
+        d, c, f = oracle.hub_columns(g, rank, hubs)
+        for i, w in enumerate(hubs):
+            for v in range(g.n):
+                e = [(dd, cc) for h, dd, cc in L[v] if h == w]
+                if e:
+                    assert (d[i, v], c[i, v], f[i, v]) == (e[0][0], e[0][1] % M64, int(e[0][1] >= M64))
+                else:
+                    assert (d[i, v], c[i, v], f[i, v]) == (oracle.UNREACHED, 0, 0)
