@@ -1,17 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the SPC hub-label path on GB300.
 
-One step = one full pass of the path on the R-MAT scale-16 workload:
-pspc_build (rank relabel, level-synchronous pull construction, finalize)
-followed by pspc_query on 10^6 uniform (s,t) pairs. Inputs are resident in
-device memory before the timed region; L2 is flushed (256 MiB write)
-between steps. Times are CUDA events on the launching stream.
+One step = one full pass of the path over the mixed pair of large graphs:
+for R-MAT scale 20 (edge factor 8) and then the 256x256 grid with 10% of
+its edges deleted, pspc_build (rank relabel, level-synchronous pull
+construction, finalize) followed by pspc_query on 10^7 uniform (s,t)
+pairs. Inputs are resident in device memory before the timed region; L2
+is flushed (256 MiB write) before every build. Times are CUDA events on the
+launching stream.
 
-Prints one JSON line. ``value`` is label entries per second of the build
+Prints one JSON line. ``value`` is label entries per second of the builds
 (whole job: summed over ranks, divided by the slowest rank's time); query
-throughput is reported beside it. ``--impl reference`` times the CPU oracle
-(the sequential hub-pushing labeler) on a bounded sample of the same
-workload instead.
+throughput, both kernels' rooflines, an end-to-end pass through the C ABI
+with host buffers, and the CPU oracle on a bounded sample are reported
+beside it. ``--impl reference`` times the CPU oracle (the sequential
+hub-pushing labeler) on a bounded sample of the same workload instead.
 
 Multi-GPU: the path does not shard without an exchange step, so N ranks run
 N independent replicas (weak scaling, no collective on the data path).
@@ -30,26 +33,41 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ORACLE_SAMPLE_HUBS = 320  # bounded CPU sample: the 320 highest-ranked hubs
+ORACLE_SAMPLE_HUBS = 320  # bounded CPU sample: at most the 320 highest-ranked hubs per graph
+ORACLE_BUILD_CAP_S = 12.0  # CPU build sample per graph, in seconds
+ORACLE_QUERY_PAIRS = {"rmat20": 400, "grid256": 100_000}  # CPU query sample (first pairs of the set)
 REFERENCE_BUDGET_S = 150.0  # whole --impl reference run, warm-up included
+
+# A workload is one graph, or a list of graphs built one after another in
+# every step.
+WORKLOAD_GRAPHS = {"cfg3": ["rmat20", "grid256"]}
 WORKLOAD_DESC = {
+    "cfg3": ("Mixed pair: R-MAT scale 20 (1,048,576 vertices), edge factor 8, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
+             "seed 1, symmetrised, self-loops and duplicates removed; and a 256x256 4-neighbour grid with 10% of "
+             "edges deleted uniformly (seed 1), largest component kept; degree-descending rank with random "
+             "tie-break (seed 3); per-graph index build plus 10^7 uniform random (s,t) pairs each (seed 2); "
+             "uint64 counts with overflow flags"),
     "rmat16": ("R-MAT scale 16 (65,536 vertices), edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
                "seed 1, symmetrised, self-loops and duplicates removed, degree-descending rank "
-               "(ties by id), int32 CSR; index build + 10^6 uniform random (s,t) pairs (seed 2)"),
+               "(ties by id), int32 CSR; index build + uniform random (s,t) pairs (seed 2)"),
 }
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="rmat16")
-    ap.add_argument("--queries", type=int, default=1_000_000)
+    ap.add_argument("--workload", default="cfg3")
+    ap.add_argument("--queries", type=int, default=10_000_000, help="query pairs per graph and step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     return ap.parse_args()
+
+
+def graph_names(workload: str):
+    return WORKLOAD_GRAPHS.get(workload, [workload])
 
 
 def dist_info():
@@ -116,24 +134,29 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-def level_kernel_traffic():
-    """DRAM bytes per launch of the level kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "k_level_rmat16.json")
+def kernel_source_sha(files) -> str:
+    """Hash of a kernel's sources (a profile is stale once they change)."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2212_00977_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+LEVEL_SOURCES = ("pspc_level.cu", "pspc_level.cuh", "pspc_internal.cuh")
+QUERY_SOURCES = ("pspc_query.cu", "pspc_internal.cuh")
+
+
+def profiled_traffic(name: str, workload: str, sources):
+    """DRAM bytes per launch from a committed ncu summary
+    (profiles/<name>_<workload>.json), if it was taken on the current
+    kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if level_kernel_source_sha() != d.get("source_sha256"):
+    if kernel_source_sha(sources) != d.get("source_sha256"):
         return None
     return d.get("dram_bytes_per_launch")
-
-
-def level_kernel_source_sha() -> str:
-    """Hash of the level kernel's sources (the profile is stale once they change)."""
-    h = hashlib.sha256()
-    for f in ("pspc_level.cu", "pspc_level.cuh", "pspc_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2212_00977_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()
 
 
 def reduce_max(vals, dist, device):
@@ -160,9 +183,24 @@ def level_algorithmic_bytes(ls):
     return 4 * ls["active_arcs"] + 12 * ls["raw_candidates"] + 12 * ls["entries"]
 
 
-def cpu_baseline(g, rank, hubs=ORACLE_SAMPLE_HUBS, time_cap_s=30.0):
-    """The oracle's labeler on the `hubs` highest-ranked hubs, stopped after
-    `time_cap_s` (large graphs); returns (entries, seconds, hubs done)."""
+def query_algorithmic_bytes(sizes, pairs, dist_out):
+    """Bytes of one query batch: per pair its 8-byte (s,t) and 11-byte
+    answer, and for s != t the hub and distance words of both labels (6 B
+    per entry) and, when reachable, the counts of at least one hub at the
+    minimum on both sides (16 B)."""
+    import numpy as np
+
+    s = pairs[:, 0].astype(np.int64)
+    t = pairs[:, 1].astype(np.int64)
+    diff = s != t
+    lab = (sizes[s] + sizes[t]).astype(np.int64)
+    reach = diff & (dist_out != 0xFFFF)
+    return int(19 * len(pairs) + 6 * lab[diff].sum() + 16 * reach.sum())
+
+
+def cpu_build_baseline(g, rank, hubs=ORACLE_SAMPLE_HUBS, time_cap_s=ORACLE_BUILD_CAP_S):
+    """The oracle's labeler on (at most) the `hubs` highest-ranked hubs,
+    stopped after `time_cap_s`; returns (entries, seconds, hubs done)."""
     import oracle
 
     t0 = time.perf_counter()
@@ -171,31 +209,61 @@ def cpu_baseline(g, rank, hubs=ORACLE_SAMPLE_HUBS, time_cap_s=30.0):
     return ix.entries, dt, ix.hubs_done
 
 
+def cpu_query_baseline(g, pairs):
+    """The oracle's SPC of the given pairs by breadth-first counting from
+    each distinct source, sources in parallel on the host cores; returns
+    (pairs, seconds, threads)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    _, _, _, th = oracle.spc_pairs(g, pairs)
+    return len(pairs), time.perf_counter() - t0, th
+
+
+def host_cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
 def run_reference(args):
     rank_id, _, world = dist_info()
     if rank_id != 0:
         return 0
     import pspc_inputs as P
 
-    g, rank, _ = P.workload(args.workload)
-    # Each step labels the top `hubs` hubs. The count is sized during the
-    # warm-up steps so that the whole run takes about REFERENCE_BUDGET_S: the
-    # labeler's time grows about with the square of the hubs it has done
-    # (each new hub's search queries the labels built so far).
-    per_step = max(0.5, min(12.0, REFERENCE_BUDGET_S / max(args.warmup + args.steps, 1)))
-    hubs = 32
+    graphs = [(name,) + tuple(P.workload(name)[:2]) for name in graph_names(args.workload)]
+    # Each step labels the top `hubs` hubs of every graph. The counts are
+    # sized during the warm-up steps so that the whole run takes about
+    # REFERENCE_BUDGET_S: the labeler's time grows about with the square of
+    # the hubs it has done (each new hub's search queries the labels built
+    # so far).
+    per_step = max(0.5, min(12.0, REFERENCE_BUDGET_S / max(args.warmup + args.steps, 1))) / len(graphs)
+    hubs = {name: 32 for name, _, _ in graphs}
     for _ in range(max(args.warmup, 1)):
-        _, t, _ = cpu_baseline(g, rank, hubs=hubs)
-        hubs = int(max(8, min(ORACLE_SAMPLE_HUBS, 4 * hubs, hubs * (per_step / max(t, 1e-3)) ** 0.5)))
+        for name, g, rank in graphs:
+            _, t, _ = cpu_build_baseline(g, rank, hubs=hubs[name], time_cap_s=0)
+            h = hubs[name]
+            hubs[name] = int(max(8, min(ORACLE_SAMPLE_HUBS, 4 * h, h * (per_step / max(t, 1e-3)) ** 0.5)))
     ent, times = 0, []
     for _ in range(args.steps):
-        e, dt, _ = cpu_baseline(g, rank, hubs=hubs)
-        ent = e
-        times.append(dt)
+        e_step, t_step = 0, 0.0
+        for name, g, rank in graphs:
+            e, dt, _ = cpu_build_baseline(g, rank, hubs=hubs[name], time_cap_s=0)
+            e_step += e
+            t_step += dt
+        ent = e_step
+        times.append(t_step)
     T = sum(times)
     value = ent * len(times) / T
-    sample = (f"hub-pushing labeler (C, 1 thread) over the {hubs} highest-ranked hubs of "
-              f"the {args.workload} graph: {ent} of its label entries per step")
+    sample = ("hub-pushing labeler (C, 1 thread) over the highest-ranked hubs of each graph: "
+              + ", ".join(f"{hubs[n]} of {n}" for n, _, _ in graphs) + f"; {ent} label entries per step")
     line = {"impl": "reference", "metric": "label entries/s (index build)", "value": value, "unit": "entries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * T / len(times), "higher_is_better": True, "scaling": "weak",
@@ -226,119 +294,163 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     pspc.load()
 
-    g, rank, pairs_fn = P.workload(args.workload)
-    pairs = pairs_fn(args.queries)
-    rp_d = torch.from_numpy(g.row_ptr).to(dev)
-    col_d = torch.from_numpy(g.col).to(dev)
-    rk_d = torch.from_numpy(rank).to(dev)
-    pairs_d = torch.from_numpy(pairs).to(dev)
-    q = len(pairs)
-    out_d = torch.empty(q, dtype=torch.uint16, device=dev)
-    out_c = torch.empty(q, dtype=torch.uint64, device=dev)
-    out_f = torch.empty(q, dtype=torch.uint8, device=dev)
+    names = graph_names(args.workload)
+    W = []  # per graph: host inputs and their device copies
+    for name in names:
+        g, rank, pairs_fn = P.workload(name)
+        pairs = pairs_fn(args.queries)
+        q = len(pairs)
+        W.append({"name": name, "g": g, "rank": rank, "pairs": pairs, "q": q,
+                  "rp": torch.from_numpy(g.row_ptr).to(dev), "col": torch.from_numpy(g.col).to(dev),
+                  "rk": torch.from_numpy(rank).to(dev), "pairs_d": torch.from_numpy(pairs).to(dev),
+                  "od": torch.empty(q, dtype=torch.uint16, device=dev),
+                  "oc": torch.empty(q, dtype=torch.uint64, device=dev),
+                  "of": torch.empty(q, dtype=torch.uint8, device=dev)})
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(timed):
+    def one(w, keep=False):
         flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e2 = torch.cuda.Event(enable_timing=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        ix = pspc.Index.build(g.n, rp_d, col_d, rk_d, stream=stream)
+        ix = pspc.Index.build(w["g"].n, w["rp"], w["col"], w["rk"], stream=stream)
         e1.record(stream)
-        ix.query(pairs_d, out_d, out_c, out_f, stream=stream)
+        ix.query(w["pairs_d"], w["od"], w["oc"], w["of"], stream=stream)
         e2.record(stream)
         e2.synchronize()
-        st = ix.stats()
-        ls = ix.level_stats()
-        ix.free()
-        return e0.elapsed_time(e1), e1.elapsed_time(e2), st, ls
+        r = {"build_ms": e0.elapsed_time(e1), "query_ms": e1.elapsed_time(e2), "st": ix.stats(),
+             "ls": ix.level_stats()}
+        if keep:
+            r["ix"] = ix
+        else:
+            ix.free()
+        return r
 
-    for _ in range(max(args.warmup, 0)):
-        step(False)
+    def step():
+        return [one(w) for w in W]
+
+    # query roofline bytes: label sizes of the finished index and the answers
+    qbytes = {}
+    for w in W:
+        r = one(w, keep=True)
+        sizes = r["ix"].label_sizes()
+        qbytes[w["name"]] = query_algorithmic_bytes(sizes, w["pairs"], w["od"].cpu().numpy())
+        r["ix"].free()
+    for _ in range(max(args.warmup - 1, 0)):
+        step()
     sampler = ClockSampler(local_rank)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    t_wall = time.perf_counter()
-    res = [step(True) for _ in range(args.steps)]
+    res = [step() for _ in range(args.steps)]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
 
-    build_ms = [r[0] for r in res]
-    query_ms = [r[1] for r in res]
-    st = res[-1][2]
-    entries = st["entries"]
-    launches_per_step = st["kernel_launches"] + st["query_kernel_launches"]
-    T_build = sum(build_ms)
-    T_query = sum(query_ms)
-    T_step = T_build + T_query
-    T_build, T_query, T_step = reduce_max([T_build, T_query, T_step], dist, dev)
     K = args.steps
-    value, qps = whole_job_rates(entries, q, K, world, T_build, T_query)
-
-    # roofline of the level kernel (gather / merge / prune / append)
-    kb = sum(level_algorithmic_bytes(l) for r in res for l in r[3])
-    kms = sum(l["kernel_ms"] for r in res for l in r[3])
-    klaunch = sum(1 for r in res for l in r[3] if l["kernel_ms"] > 0)
+    entries = sum(r["st"]["entries"] for r in res[-1])
+    q_step = sum(w["q"] for w in W)
+    T_build = sum(r["build_ms"] for st in res for r in st)
+    T_query = sum(r["query_ms"] for st in res for r in st)
+    T_build, T_query = reduce_max([T_build, T_query], dist, dev)
+    value, qps = whole_job_rates(entries, q_step, K, world, T_build, T_query)
+    launches_per_step = sum(r["st"]["kernel_launches"] + r["st"]["query_kernel_launches"] for r in res[-1])
     peak, peak_kind = measured_peak_hbm()
+
+    # roofline of the level kernel (gather / merge / prune / append), over all graphs
+    per_graph = {}
+    kb = kms = kl = 0.0
+    qb = qms = 0.0
+    for gi, w in enumerate(W):
+        b = sum(level_algorithmic_bytes(l) for st in res for l in st[gi]["ls"])
+        t = sum(l["kernel_ms"] for st in res for l in st[gi]["ls"])
+        nl = sum(1 for st in res for l in st[gi]["ls"] if l["kernel_ms"] > 0)
+        bq = qbytes[w["name"]] * K
+        tq = sum(st[gi]["query_ms"] for st in res)
+        kb, kms, kl, qb, qms = kb + b, kms + t, kl + nl, qb + bq, qms + tq
+        r = res[-1][gi]
+        per_graph[w["name"]] = {
+            "n": w["g"].n, "arcs": w["g"].arcs, "entries": r["st"]["entries"], "levels": r["st"]["levels"],
+            "overflow_entries": r["st"]["overflow_entries"],
+            "build_ms": sum(st[gi]["build_ms"] for st in res) / K, "query_ms": tq / K,
+            "entries_per_s": r["st"]["entries"] * K / (sum(st[gi]["build_ms"] for st in res) / 1e3),
+            "queries_per_s": w["q"] * K / (tq / 1e3),
+            "k_level_ms": t / K, "k_level_gbs": b / (t / 1e3) / 1e9 if t else 0.0,
+            "query_gbs": bq / (tq / 1e3) / 1e9 if tq else 0.0,
+            "landmark_ms": r["st"]["landmark_ms"]}
     achieved = kb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
-    traffic = level_kernel_traffic() if args.workload == "rmat16" else None  # the capture is of R-MAT 16
+    achieved_q = qb / (qms / 1e3) / 1e9 if qms > 0 else 0.0
+    traffic = profiled_traffic("k_level", args.workload, LEVEL_SOURCES)
+    traffic_q = profiled_traffic("k_query", args.workload, QUERY_SOURCES)
 
     line = {"metric": "label entries/s (index build)", "value": value, "unit": "entries/s", "n_gpus": world,
-            "steps": K, "warmup": args.warmup, "ms_per_step": T_step / K, "higher_is_better": True,
+            "steps": K, "warmup": args.warmup, "ms_per_step": (T_build + T_query) / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "n": g.n, "arcs": g.arcs,
-                       "queries_per_step": q, "l2": "flushed: 256 MiB device write before every step",
+            "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "graphs": names,
+                       "queries_per_step": q_step, "l2": "flushed: 256 MiB device write before every build",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "build_ms": T_build / K, "query_ms": T_query / K, "queries_per_s": qps,
-            "entries": entries, "levels": st["levels"], "landmarks": st["landmarks"],
-            "landmark_ms": st["landmark_ms"],
+            "build_ms": T_build / K, "query_ms": T_query / K, "queries_per_s": qps, "entries": entries,
+            "per_graph": per_graph,
             "roofline": {"kernel": "k_level (pull gather + count merge + prune + append)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if peak else None,
-                         "peak_kind": peak_kind,
+                         "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
                          "traffic": traffic,
-                         "bytes_per_step": kb / K, "kernel_ms_per_step": kms / K,
-                         "launches_per_step": klaunch / K},
-            "level_kernel_ms": [round(l["kernel_ms"], 3) for l in res[-1][3]],
-            "level_ms": [round(l["ms"], 3) for l in res[-1][3]],
+                         "dram_gbs": (traffic * kl / (kms / 1e3) / 1e9) if (traffic and kms) else None,
+                         "bytes_per_step": kb / K, "kernel_ms_per_step": kms / K, "launches_per_step": kl / K},
+            "roofline_query": {"kernel": "query call: source grouping + merge-join (Eq. (1)-(2))", "bound": "hbm",
+                               "achieved": achieved_q, "peak": peak, "unit": "GB/s",
+                               "frac": achieved_q / peak if peak else None, "peak_kind": peak_kind,
+                               "traffic": traffic_q, "bytes_per_step": qb / K, "ms_per_step": qms / K},
             "gpu_launches": launches_per_step * K,
             "clocks": clocks}
 
     if rank_id == 0 and world == 1 and args.e2e_steps > 0:
-        # end to end through the public API with host buffers
-        e2e_b, e2e_q = [], []
-        h2d = g.row_ptr.nbytes + g.col.nbytes + rank.nbytes + pairs.nbytes
-        d2h = q * (2 + 8 + 1)
-        for i in range(args.e2e_steps + 1):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ix = pspc.Index.from_graph(g, rank)
-            t1 = time.perf_counter()
-            d, c, f = ix.query(pairs)
-            t2 = time.perf_counter()
-            ix.free()
-            if i:  # first one is a warm-up
-                e2e_b.append(t1 - t0)
-                e2e_q.append(t2 - t1)
-        line["e2e"] = {"value": entries / statistics.mean(e2e_b), "unit": "entries/s",
-                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                       "queries_per_s": q / statistics.mean(e2e_q),
-                       "step_s": statistics.mean(e2e_b) + statistics.mean(e2e_q)}
-    if rank_id == 0 and world == 1:
-        if not args.no_cpu_baseline:
-            ent, dt, done = cpu_baseline(g, rank)
-            line["cpu_baseline"] = {
-                "value": ent / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
-                "sample": (f"hub-pushing labeler (C, 1 thread) over the {done} highest-ranked "
-                           f"hubs of the same graph: {ent} label entries in {dt:.1f} s")}
+        # end to end through the public API with host buffers: the CSR,
+        # rank and pairs are copied in and the answers out inside the calls
+        tb = tq = 0.0
+        for _ in range(args.e2e_steps):
+            for w in W:
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ix = pspc.Index.from_graph(w["g"], w["rank"])
+                t1 = time.perf_counter()
+                d, c, f = ix.query(w["pairs"])
+                t2 = time.perf_counter()
+                ix.free()
+                tb += t1 - t0
+                tq += t2 - t1
+        h2d = sum(w["g"].row_ptr.nbytes + w["g"].col.nbytes + w["rank"].nbytes + w["pairs"].nbytes for w in W)
+        d2h = q_step * (2 + 8 + 1)
+        E = args.e2e_steps
+        line["e2e"] = {"value": entries * E / tb, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "queries_per_s": q_step * E / tq, "step_s": (tb + tq) / E}
+    if rank_id == 0 and world == 1 and not args.no_cpu_baseline:
+        eb = tbs = 0.0
+        done = []
+        for w in W:
+            e, dt, h = cpu_build_baseline(w["g"], w["rank"])
+            eb, tbs = eb + e, tbs + dt
+            done.append(f"{h} hubs of {w['name']} ({e} entries, {dt:.1f} s)")
+        line["cpu_baseline"] = {
+            "value": eb / tbs, "unit": "entries/s", "cores": 1, "kind": "oracle",
+            "sample": "hub-pushing labeler (C, 1 thread) over the highest-ranked hubs of each graph, stopped "
+                      f"after {ORACLE_BUILD_CAP_S:.0f} s per graph: " + "; ".join(done)}
+        nq = tqs = 0.0
+        qdone, threads = [], 1
+        for w in W:
+            k = min(w["q"], ORACLE_QUERY_PAIRS.get(w["name"], 10_000))
+            m, dt, threads = cpu_query_baseline(w["g"], w["pairs"][:k])
+            nq, tqs = nq + m, tqs + dt
+            qdone.append(f"{m} pairs of {w['name']} in {dt:.1f} s")
+        line["cpu_baseline_query"] = {
+            "value": nq / tqs, "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "cpu": host_cpu_model(), "nproc": os.cpu_count(),
+            "sample": "SPC by breadth-first path counting from each distinct source (the definition), sources "
+                      "in parallel on all host cores, over the first pairs of each graph's set: "
+                      + "; ".join(qdone)}
     if rank_id == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -335,6 +335,17 @@ class Index:
             raise PSPCError(rc, "pspc_export_vertices")
         return off, hub, dist, cnt, ovf
 
+    def label_sizes(self, verts=None) -> np.ndarray:
+        """Entries of L(v) for the given caller vertices (all by default),
+        through pspc_export_vertices with only the offsets requested."""
+        lib = load()
+        v = np.arange(self.n, dtype=np.int32) if verts is None else np.ascontiguousarray(verts, dtype=np.int32)
+        off = np.empty(len(v) + 1, np.int64)
+        rc = lib.pspc_export_vertices(self._h, _ptr(v), len(v), _ptr(off), None, None, None, None)
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_export_vertices")
+        return np.diff(off)
+
     def hub_column(self, w: int):
         """pspc_hub_column: (dist, cnt, ovf) of hub w in every label."""
         d = np.empty(self.n, np.uint16)
