@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--queries", type=int, default=10_000_000, help="query pairs per graph and step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cfg2-steps", type=int, default=10, help="timed passes of the R-MAT 16 extra figures")
     return ap.parse_args()
 
 
@@ -275,42 +276,39 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
-    import numpy as np
-    import torch
+class Workload:
+    """The graphs of a workload with their inputs resident on the device,
+    and the timed pass of the path over them."""
 
-    import paper_2212_00977_gb300 as pspc
-    import pspc_inputs as P
+    def __init__(self, names, queries, dev):
+        import torch
 
-    rank_id, local_rank, world = dist_info()
-    if not torch.cuda.is_available():
-        raise RuntimeError("bench.py needs a CUDA device")
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+        import pspc_inputs as P
 
-        dist.init_process_group("nccl", device_id=dev)
-    pspc.load()
+        self.torch = torch
+        self.dev = dev
+        self.W = []
+        for name in names:
+            g, rank, pairs_fn = P.workload(name)
+            pairs = pairs_fn(queries)
+            q = len(pairs)
+            self.W.append({"name": name, "g": g, "rank": rank, "pairs": pairs, "q": q,
+                           "rp": torch.from_numpy(g.row_ptr).to(dev), "col": torch.from_numpy(g.col).to(dev),
+                           "rk": torch.from_numpy(rank).to(dev), "pairs_d": torch.from_numpy(pairs).to(dev),
+                           "od": torch.empty(q, dtype=torch.uint16, device=dev),
+                           "oc": torch.empty(q, dtype=torch.uint64, device=dev),
+                           "of": torch.empty(q, dtype=torch.uint8, device=dev)})
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream(dev)
+        self.qbytes = {}
 
-    names = graph_names(args.workload)
-    W = []  # per graph: host inputs and their device copies
-    for name in names:
-        g, rank, pairs_fn = P.workload(name)
-        pairs = pairs_fn(args.queries)
-        q = len(pairs)
-        W.append({"name": name, "g": g, "rank": rank, "pairs": pairs, "q": q,
-                  "rp": torch.from_numpy(g.row_ptr).to(dev), "col": torch.from_numpy(g.col).to(dev),
-                  "rk": torch.from_numpy(rank).to(dev), "pairs_d": torch.from_numpy(pairs).to(dev),
-                  "od": torch.empty(q, dtype=torch.uint16, device=dev),
-                  "oc": torch.empty(q, dtype=torch.uint64, device=dev),
-                  "of": torch.empty(q, dtype=torch.uint8, device=dev)})
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    def one(self, w, keep=False):
+        """Build one graph's index, then answer its pairs (CUDA events on
+        the launching stream; L2 flushed first)."""
+        import paper_2212_00977_gb300 as pspc
 
-    def one(w, keep=False):
-        flush.fill_(1)
+        torch, stream = self.torch, self.stream
+        self.flush.fill_(1)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         ix = pspc.Index.build(w["g"].n, w["rp"], w["col"], w["rk"], stream=stream)
@@ -326,24 +324,83 @@ def run_ours(args):
             ix.free()
         return r
 
-    def step():
-        return [one(w) for w in W]
+    def step(self):
+        return [self.one(w) for w in self.W]
 
-    # query roofline bytes: label sizes of the finished index and the answers
-    qbytes = {}
-    for w in W:
-        r = one(w, keep=True)
-        sizes = r["ix"].label_sizes()
-        qbytes[w["name"]] = query_algorithmic_bytes(sizes, w["pairs"], w["od"].cpu().numpy())
-        r["ix"].free()
-    for _ in range(max(args.warmup - 1, 0)):
-        step()
+    def warm(self, warmup):
+        """Warm-up passes; the first also fixes each graph's query bytes
+        (label sizes of the finished index and the answers)."""
+        for w in self.W:
+            r = self.one(w, keep=True)
+            sizes = r["ix"].label_sizes()
+            self.qbytes[w["name"]] = query_algorithmic_bytes(sizes, w["pairs"], w["od"].cpu().numpy())
+            r["ix"].free()
+        for _ in range(max(warmup - 1, 0)):
+            self.step()
+
+    def summary(self, res, peak, peak_kind, workload):
+        """Per-graph figures and the two rooflines of timed passes `res`."""
+        K = len(res)
+        per_graph = {}
+        kb = kms = kl = qb = qms = 0.0
+        for gi, w in enumerate(self.W):
+            b = sum(level_algorithmic_bytes(l) for st in res for l in st[gi]["ls"])
+            t = sum(l["kernel_ms"] for st in res for l in st[gi]["ls"])
+            nl = sum(1 for st in res for l in st[gi]["ls"] if l["kernel_ms"] > 0)
+            bq = self.qbytes[w["name"]] * K
+            tq = sum(st[gi]["query_ms"] for st in res)
+            tb = sum(st[gi]["build_ms"] for st in res)
+            kb, kms, kl, qb, qms = kb + b, kms + t, kl + nl, qb + bq, qms + tq
+            r = res[-1][gi]
+            per_graph[w["name"]] = {
+                "n": w["g"].n, "arcs": w["g"].arcs, "entries": r["st"]["entries"], "levels": r["st"]["levels"],
+                "overflow_entries": r["st"]["overflow_entries"], "queries": w["q"],
+                "build_ms": tb / K, "query_ms": tq / K,
+                "entries_per_s": r["st"]["entries"] * K / (tb / 1e3), "queries_per_s": w["q"] * K / (tq / 1e3),
+                "k_level_ms": t / K, "k_level_gbs": b / (t / 1e3) / 1e9 if t else 0.0,
+                "query_gbs": bq / (tq / 1e3) / 1e9 if tq else 0.0, "landmark_ms": r["st"]["landmark_ms"]}
+        achieved = kb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+        achieved_q = qb / (qms / 1e3) / 1e9 if qms > 0 else 0.0
+        traffic = profiled_traffic("k_level", workload, LEVEL_SOURCES)
+        traffic_q = profiled_traffic("k_query", workload, QUERY_SOURCES)
+        roof = {"kernel": "k_level (pull gather + count merge + prune + append)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                "peak_kind": peak_kind, "traffic": traffic,
+                "dram_gbs": (traffic * kl / (kms / 1e3) / 1e9) if (traffic and kms) else None,
+                "bytes_per_step": kb / K, "kernel_ms_per_step": kms / K, "launches_per_step": kl / K}
+        roof_q = {"kernel": "query call: source grouping + merge-join (Eq. (1)-(2))", "bound": "hbm",
+                  "achieved": achieved_q, "peak": peak, "unit": "GB/s", "frac": achieved_q / peak if peak else None,
+                  "peak_kind": peak_kind, "traffic": traffic_q, "bytes_per_step": qb / K, "ms_per_step": qms / K}
+        return per_graph, roof, roof_q
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2212_00977_gb300 as pspc
+
+    rank_id, local_rank, world = dist_info()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    pspc.load()
+
+    names = graph_names(args.workload)
+    wl = Workload(names, args.queries, dev)
+    W = wl.W
+    wl.warm(args.warmup)
     sampler = ClockSampler(local_rank)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    res = [step() for _ in range(args.steps)]
+    res = [wl.step() for _ in range(args.steps)]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -358,32 +415,7 @@ def run_ours(args):
     value, qps = whole_job_rates(entries, q_step, K, world, T_build, T_query)
     launches_per_step = sum(r["st"]["kernel_launches"] + r["st"]["query_kernel_launches"] for r in res[-1])
     peak, peak_kind = measured_peak_hbm()
-
-    # roofline of the level kernel (gather / merge / prune / append), over all graphs
-    per_graph = {}
-    kb = kms = kl = 0.0
-    qb = qms = 0.0
-    for gi, w in enumerate(W):
-        b = sum(level_algorithmic_bytes(l) for st in res for l in st[gi]["ls"])
-        t = sum(l["kernel_ms"] for st in res for l in st[gi]["ls"])
-        nl = sum(1 for st in res for l in st[gi]["ls"] if l["kernel_ms"] > 0)
-        bq = qbytes[w["name"]] * K
-        tq = sum(st[gi]["query_ms"] for st in res)
-        kb, kms, kl, qb, qms = kb + b, kms + t, kl + nl, qb + bq, qms + tq
-        r = res[-1][gi]
-        per_graph[w["name"]] = {
-            "n": w["g"].n, "arcs": w["g"].arcs, "entries": r["st"]["entries"], "levels": r["st"]["levels"],
-            "overflow_entries": r["st"]["overflow_entries"],
-            "build_ms": sum(st[gi]["build_ms"] for st in res) / K, "query_ms": tq / K,
-            "entries_per_s": r["st"]["entries"] * K / (sum(st[gi]["build_ms"] for st in res) / 1e3),
-            "queries_per_s": w["q"] * K / (tq / 1e3),
-            "k_level_ms": t / K, "k_level_gbs": b / (t / 1e3) / 1e9 if t else 0.0,
-            "query_gbs": bq / (tq / 1e3) / 1e9 if tq else 0.0,
-            "landmark_ms": r["st"]["landmark_ms"]}
-    achieved = kb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
-    achieved_q = qb / (qms / 1e3) / 1e9 if qms > 0 else 0.0
-    traffic = profiled_traffic("k_level", args.workload, LEVEL_SOURCES)
-    traffic_q = profiled_traffic("k_query", args.workload, QUERY_SOURCES)
+    per_graph, roof, roof_q = wl.summary(res, peak, peak_kind, args.workload)
 
     line = {"metric": "label entries/s (index build)", "value": value, "unit": "entries/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": (T_build + T_query) / K, "higher_is_better": True,
@@ -392,27 +424,26 @@ def run_ours(args):
                        "queries_per_step": q_step, "l2": "flushed: 256 MiB device write before every build",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "build_ms": T_build / K, "query_ms": T_query / K, "queries_per_s": qps, "entries": entries,
-            "per_graph": per_graph,
-            "roofline": {"kernel": "k_level (pull gather + count merge + prune + append)", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
-                         "traffic": traffic,
-                         "dram_gbs": (traffic * kl / (kms / 1e3) / 1e9) if (traffic and kms) else None,
-                         "bytes_per_step": kb / K, "kernel_ms_per_step": kms / K, "launches_per_step": kl / K},
-            "roofline_query": {"kernel": "query call: source grouping + merge-join (Eq. (1)-(2))", "bound": "hbm",
-                               "achieved": achieved_q, "peak": peak, "unit": "GB/s",
-                               "frac": achieved_q / peak if peak else None, "peak_kind": peak_kind,
-                               "traffic": traffic_q, "bytes_per_step": qb / K, "ms_per_step": qms / K},
-            "gpu_launches": launches_per_step * K,
-            "clocks": clocks}
+            "per_graph": per_graph, "roofline": roof, "roofline_query": roof_q,
+            "gpu_launches": launches_per_step * K, "clocks": clocks}
 
+    if rank_id == 0 and world == 1 and args.workload == "cfg3" and args.cfg2_steps > 0:
+        # the R-MAT 16 workload (10^6 pairs) as extra figures, outside the
+        # timed region of the line's value
+        w2 = Workload(["rmat16"], 1_000_000, dev)
+        w2.warm(3)
+        r2 = [w2.step() for _ in range(args.cfg2_steps)]
+        pg2, roof2, roofq2 = w2.summary(r2, peak, peak_kind, "rmat16")
+        line["cfg2"] = {"workload": WORKLOAD_DESC["rmat16"] + ", 10^6 pairs", "steps": args.cfg2_steps,
+                        "warmup": 3, **pg2["rmat16"], "roofline": roof2, "roofline_query": roofq2}
+        del w2
     if rank_id == 0 and world == 1 and args.e2e_steps > 0:
         # end to end through the public API with host buffers: the CSR,
         # rank and pairs are copied in and the answers out inside the calls
         tb = tq = 0.0
         for _ in range(args.e2e_steps):
             for w in W:
-                flush.fill_(1)
+                wl.flush.fill_(1)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 ix = pspc.Index.from_graph(w["g"], w["rank"])

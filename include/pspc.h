@@ -98,8 +98,9 @@ typedef struct {
                                 every vertex (two bytes each) let the prune
                                 step drop a candidate h of u at level d at
                                 once when sd(u,l) + sd(l,h) < d for some
-                                landmark l. 0 = default (K = 32), -1 = off,
-                                1..64 = K. Results do not depend on it */
+                                landmark l. 0 = default (K = 64), -1 = off,
+                                1..64 = K; levels below 16 test at most
+                                the first 32. Results do not depend on it */
     int32_t reduce_shell;    /* 1: reduction by 1-shell (Section "Index
                                 Size Reduction"): vertices of degree 1 are
                                 peeled repeatedly, the index is built on the

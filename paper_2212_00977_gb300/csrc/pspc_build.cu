@@ -914,6 +914,9 @@ struct Builder {
         A.comp_base = comp_base;
         A.lmk = out.lmk;
         A.lmk_stride = out.lmk_stride;
+        // shallow levels test the first kLmkShallow landmarks only: their
+        // short distances seldom prove survival, and half the row is read
+        A.lmk_words = d < kLmkDeepLevel ? std::min(out.lmk_stride / 16, 2 * kLmkShallow / 16) : out.lmk_stride / 16;
         if (hstt->n_smem > 0) {
             A.items = items;
             A.n_items = hstt->n_smem;
@@ -1319,7 +1322,7 @@ static void fill_defaults(pspc_opts& o, const pspc_opts* user) {
     if (o.cand_capacity <= 0) o.cand_capacity = 4096;
     if (o.label_capacity <= 0) o.label_capacity = 8192;
     if (o.max_levels <= 0) o.max_levels = kMaxDist;
-    if (o.landmarks == 0) o.landmarks = 32;
+    if (o.landmarks == 0) o.landmarks = 64;
 }
 
 static bool opts_ok(const pspc_opts& o) {

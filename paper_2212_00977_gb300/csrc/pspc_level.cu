@@ -369,12 +369,64 @@ __device__ long long block_excl_scan_popc(const uint32_t* bits, uint32_t* wp, ui
     return total;
 }
 
-// Rule 2 for the candidates list[0..M): G lanes per candidate h. Lane j
-// reads the descriptor of level k0 + j of L(h) (levels 1..d-2, G at a time);
-// the lengths are prefix-summed over the group and the concatenated entries
+// Rule 2 over levels klo..khi of L(h) for one candidate h, by one group of
+// G lanes. Lane j reads the descriptor of level k0 + j (G at a time); the
+// lengths are prefix-summed over the group and the concatenated entries
 // scanned in level order, kProbeUnroll loads in flight per lane. The level of
 // entry i is the last lane whose exclusive prefix is <= i (a binary search
 // by shuffles). An entry x of level k is a witness iff d_u(x) <= d-1-k.
+// Returns whether the group found a witness; it also stops (returning
+// false) once *stop, shared with other groups scanning other levels of the
+// same candidate, is set.
+template <int G, class Map>
+__device__ bool scan_levels(const Map& mp, const uint64_t* __restrict__ seg, const uint32_t* __restrict__ hub_arena,
+                            int64_t n, int d, uint32_t h, int klo, int khi, const int* stop) {
+    auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+    const int gl = tile.thread_rank();
+    bool pruned = false, halt = false;
+    for (int k0 = klo; k0 <= khi && !pruned && !halt; k0 += G) {
+        const int k = k0 + gl;
+        const uint64_t s = k <= khi ? __ldg(seg + (int64_t)k * n + h) : 0ull;
+        const uint32_t len = seg_len(s);
+        const unsigned long long start = seg_start(s);
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const uint32_t t = tile.shfl_up(incl, o);
+            if (gl >= o) incl += t;
+        }
+        const uint32_t excl = incl - len;
+        const uint32_t total = tile.shfl(incl, G - 1);
+        for (uint32_t b = 0; b < total && !pruned && !halt; b += G * kProbeUnroll) {
+            uint32_t x[kProbeUnroll];
+            int thr[kProbeUnroll];
+#pragma unroll
+            for (int t = 0; t < kProbeUnroll; ++t) {
+                const uint32_t i = b + t * G + gl;
+                int j = 0;
+#pragma unroll
+                for (int step = G >> 1; step > 0; step >>= 1) {
+                    const uint32_t e = tile.shfl(excl, j + step);
+                    if (e <= i) j += step;
+                }
+                const unsigned long long sj = tile.shfl(start, j);
+                const uint32_t ej = tile.shfl(excl, j);
+                thr[t] = d - 1 - (k0 + j);
+                x[t] = i < total ? (__ldg(hub_arena + sj + (i - ej)) & kHubMask) : kEmpty;
+            }
+            bool hit = false;
+#pragma unroll
+            for (int t = 0; t < kProbeUnroll; ++t)
+                if (x[t] != kEmpty) hit |= mp.within(x[t], thr[t]);
+            pruned = tile.any(hit);
+            if (stop) halt = tile.any(*(volatile const int*)stop != 0);
+        }
+    }
+    return pruned;
+}
+
+// Rule 2 for the candidates list[0..M): G lanes per candidate h take
+// candidates from a shared counter and scan levels 1..d-2 of L(h).
 template <int G, class Map>
 __device__ void prune_candidates(const Map& mp, const uint64_t* __restrict__ seg,
                                  const uint32_t* __restrict__ hub_arena, int64_t n, int d, uint32_t* list,
@@ -389,46 +441,55 @@ __device__ void prune_candidates(const Map& mp, const uint64_t* __restrict__ seg
         const uint32_t slot = list[c];
         if (slot & kProvenBit) continue;
         const uint32_t h = ckeys[slot] & kHubMask;
-        bool pruned = false;
-        for (int k0 = 1; k0 <= d - 2 && !pruned; k0 += G) {
-            const int k = k0 + gl;
-            const uint64_t s = k <= d - 2 ? __ldg(seg + (int64_t)k * n + h) : 0ull;
-            const uint32_t len = seg_len(s);
-            const unsigned long long start = seg_start(s);
-            uint32_t incl = len;
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) {
-                const uint32_t t = tile.shfl_up(incl, o);
-                if (gl >= o) incl += t;
-            }
-            const uint32_t excl = incl - len;
-            const uint32_t total = tile.shfl(incl, G - 1);
-            for (uint32_t b = 0; b < total && !pruned; b += G * kProbeUnroll) {
-                uint32_t x[kProbeUnroll];
-                int thr[kProbeUnroll];
-#pragma unroll
-                for (int t = 0; t < kProbeUnroll; ++t) {
-                    const uint32_t i = b + t * G + gl;
-                    int j = 0;
-#pragma unroll
-                    for (int step = G >> 1; step > 0; step >>= 1) {
-                        const uint32_t e = tile.shfl(excl, j + step);
-                        if (e <= i) j += step;
-                    }
-                    const unsigned long long sj = tile.shfl(start, j);
-                    const uint32_t ej = tile.shfl(excl, j);
-                    thr[t] = d - 1 - (k0 + j);
-                    x[t] = i < total ? (__ldg(hub_arena + sj + (i - ej)) & kHubMask) : kEmpty;
-                }
-                bool hit = false;
-#pragma unroll
-                for (int t = 0; t < kProbeUnroll; ++t)
-                    if (x[t] != kEmpty) hit |= mp.within(x[t], thr[t]);
-                pruned = tile.any(hit);
-            }
-        }
+        const bool pruned = scan_levels<G>(mp, seg, hub_arena, n, d, h, 1, d - 2, nullptr);
         if (pruned && gl == 0) list[c] = slot | kPrunedBit;
     }
+}
+
+// Rule 2 when fewer candidates remain to be scanned than the CTA has warps
+// (P < 16: the deep levels of high-diameter graphs, where each scan is
+// long): the warps form P' >= P groups of wpc = 16 / P' warps, group g takes
+// the g-th candidate still undecided, and its warps split levels 1..d-2
+// into wpc contiguous ranges. A warp that finds a witness sets the group's
+// flag, and the others stop at their next step. Every warp reaches the
+// barriers (the call is made by the whole CTA).
+template <class Map>
+__device__ void prune_split(const Map& mp, const uint64_t* __restrict__ seg, const uint32_t* __restrict__ hub_arena,
+                            int64_t n, int d, uint32_t* list, const uint32_t* ckeys, int M, int P, int* s_flag) {
+    constexpr int kWarps = kLevelThreads / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int wpc = 1;
+    while (wpc * 2 * P <= kWarps) wpc *= 2;
+    const int groups = kWarps / wpc, g = warp / wpc, j = warp % wpc;
+    if (tid < kWarps) s_flag[tid] = 0;
+    __syncthreads();
+    // position in list of the g-th candidate that is not proven
+    int c = -1;
+    if (g < P) {
+        int seen = 0;
+        for (int base = 0; base < M && c < 0; base += 32) {
+            const int i = base + lane;
+            const bool open = i < M && !(list[i] & kProvenBit);
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, open);
+            const int cnt = __popc(bal);
+            if (seen + cnt > g) {
+                unsigned m = bal;
+                for (int r = g - seen; r > 0; --r) m &= m - 1;
+                c = base + __ffs(m) - 1;
+            }
+            seen += cnt;
+        }
+    }
+    if (c >= 0) {
+        const uint32_t h = ckeys[list[c] & kSlotMask] & kHubMask;
+        const int levels = d - 2;
+        const int klo = 1 + (int)((int64_t)levels * j / wpc), khi = (int)((int64_t)levels * (j + 1) / wpc);
+        if (klo <= khi && scan_levels<32>(mp, seg, hub_arena, n, d, h, klo, khi, &s_flag[g]) && lane == 0)
+            atomicExch(&s_flag[g], 1);
+    }
+    __syncthreads();
+    if (c >= 0 && j == 0 && lane == 0 && s_flag[g]) list[c] |= kPrunedBit;
+    (void)groups;
 }
 
 // Rule 2 level by level: G lanes per candidate scan L_1(h), then L_2(h), ...
@@ -517,10 +578,10 @@ __device__ void prune_by_level(const Map& mp, const uint64_t* __restrict__ seg,
 template <class Map>
 __device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, const uint32_t* hub_arena, int64_t n,
                                           int d, uint32_t* list, const uint32_t* ckeys, int M, int to_scan,
-                                          int* next, const uint64_t* useg) {
+                                          int* next, const uint64_t* useg, int* s_flag) {
     if (to_scan >= 64) prune_by_level<8>(mp, seg, hub_arena, n, d, list, ckeys, M, next, useg);
     else if (to_scan >= 16) prune_candidates<16>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
-    else prune_candidates<32>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
+    else prune_split(mp, seg, hub_arena, n, d, list, ckeys, M, to_scan, s_flag);
 }
 
 // Landmark filter (Section "Landmark-Based Filtering"). For a candidate h
@@ -540,7 +601,7 @@ __device__ int landmark_filter(const LevelArgs& A, const uint32_t* s_lmk, int d,
                                const uint32_t* ckeys, int M, int* s_wcnt, int* s_kept, int* n_proven) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t dd = (uint32_t)d * 0x00010001u;  // d <= 32767 in both halfwords
-    const int words = A.lmk_stride / 16;
+    const int words = A.lmk_words;
     int kept = 0, proven = 0;
     for (int base = 0; base < M; base += kLevelThreads) {
         const int c = base + tid;
@@ -908,10 +969,10 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             __syncthreads();
             const uint64_t* useg = useg_on ? s_useg : nullptr;
             if constexpr (kMap == kMapBitmap)
-                prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg);
+                prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
             else if constexpr (kMap == kMapHash)
-                prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg);
-            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg);
+                prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
+            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
             __syncthreads();
         }
         M = M_scan;  // list[0..M) now holds every candidate that can survive

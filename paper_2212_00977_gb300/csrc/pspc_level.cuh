@@ -14,6 +14,8 @@ constexpr int kLevelThreads = 512;
 constexpr int kArcChunk = kLevelThreads;  // arcs staged per gather chunk
 constexpr int kBuckets = 64;
 constexpr size_t kBitmapBudget = 40 * 1024;  // on-chip bytes for the level bitmaps
+constexpr int kLmkShallow = 32;    // landmarks the filter tests below level kLmkDeepLevel
+constexpr int kLmkDeepLevel = 16;  // from this level on, the filter tests every landmark
 
 struct LevelStatus {
     unsigned long long raw_total;
@@ -72,6 +74,7 @@ struct LevelArgs {
     size_t gscratch_stride;
     const uint8_t* lmk;   // [n][lmk_stride] bytes of uint16 landmark distances, or NULL (no filter)
     int lmk_stride;       // bytes per row: a multiple of 16, <= 128
+    int lmk_words;        // 16-byte words of each row the filter tests at this level
 };
 
 // Table layout (on chip, or in per-CTA device scratch). The map region also
