@@ -136,6 +136,9 @@ typedef struct {
     int64_t landmark_pruned;   /* candidates the landmark filter dropped */
     int64_t landmark_proven;   /* candidates the landmarks proved to survive
                                   (the rest went through the label scan) */
+    int64_t offchip_vertices;  /* vertices whose tables did not fit on chip
+                                  and ran in device memory */
+    float offchip_ms;          /* device time of their kernel launches */
 } pspc_level_stat_t;
 
 typedef struct {

@@ -61,7 +61,8 @@ class LevelStat(ctypes.Structure):
     _fields_ = [("raw_candidates", ctypes.c_int64), ("unique_candidates", ctypes.c_int64),
                 ("entries", ctypes.c_int64), ("active_vertices", ctypes.c_int64),
                 ("active_arcs", ctypes.c_int64), ("ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
-                ("landmark_pruned", ctypes.c_int64), ("landmark_proven", ctypes.c_int64)]
+                ("landmark_pruned", ctypes.c_int64), ("landmark_proven", ctypes.c_int64),
+                ("offchip_vertices", ctypes.c_int64), ("offchip_ms", ctypes.c_float)]
 
 
 class Stats(ctypes.Structure):

@@ -519,6 +519,8 @@ struct LevelPlan {
     int64_t label_limit = 0;
     size_t smem_bytes = 0;
     int occupancy = 0;
+    size_t light_smem_bytes = 0;  // light vertices: kLightThreads CTAs, segment-search map
+    int light_occupancy = 0;
 };
 
 struct Builder {
@@ -570,6 +572,7 @@ struct Builder {
     Index out;
     cudaEvent_t ek0 = nullptr, ek1 = nullptr;
     float kernel_ms = 0.f;  // level-kernel time of the current level
+    float offchip_ms = 0.f; // of which the off-chip variant
     int smem_optin = 0;
 
     ~Builder() {
@@ -918,20 +921,43 @@ struct Builder {
         // short distances seldom prove survival, and half the row is read
         A.lmk_words = d < kLmkDeepLevel ? std::min(out.lmk_stride / 16, 2 * kLmkShallow / 16) : out.lmk_stride / 16;
         if (hstt->n_smem > 0) {
-            A.items = items;
-            A.n_items = hstt->n_smem;
-            A.work = &stt->work_smem;
-            A.cap_c_max = plan.cap_c;
-            A.cap_u_max = plan.cap_u;
-            A.bm_words = plan.bm_words;
-            int grid = std::min(hstt->n_smem, sms * plan.occupancy);
-            if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
+            // Items are bucketed heaviest first. Light vertices (fewer than
+            // 2^kLightBucket pulled entries) run in small CTAs with small
+            // tables and the segment-search map, so that many of them share
+            // an SM; the others in full-size CTAs.
+            int n_light = 0;
+            for (int b = 0; b < kLightBucket; ++b) n_light += hstt->bucket_cnt[b];
+            const int n_heavy = hstt->n_smem - n_light;
             A.granular = o.granular ? 1 : 0;
-            if (o.granular) grid = hstt->n_smem;
             cudaEventRecord(ek0, st);
-            cudaError_t e = launch_level(plan.map_kind, false, grid, plan.smem_bytes, A, st);
+            cudaError_t e = cudaSuccess;
+            if (n_heavy > 0) {
+                A.items = items;
+                A.n_items = n_heavy;
+                A.work = &stt->work_smem;
+                A.cap_c_max = plan.cap_c;
+                A.cap_u_max = plan.cap_u;
+                A.bm_words = plan.bm_words;
+                int grid = std::min(n_heavy, sms * plan.occupancy);
+                if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
+                if (o.granular) grid = n_heavy;
+                e = launch_level(plan.map_kind, false, grid, plan.smem_bytes, A, st);
+                out.launches += 1;
+            }
+            if (e == cudaSuccess && n_light > 0) {
+                A.items = items + n_heavy;
+                A.n_items = n_light;
+                A.work = &stt->work_light;
+                A.cap_c_max = kLightCap;
+                A.cap_u_max = plan.cap_u;
+                A.bm_words = plan.bm_words;
+                int grid = std::min(n_light, sms * plan.light_occupancy);
+                if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
+                if (o.granular) grid = n_light;
+                e = launch_level(kMapSeg, false, grid, plan.light_smem_bytes, A, st, kLightThreads);
+                out.launches += 1;
+            }
             cudaEventRecord(ek1, st);
-            out.launches += 1;
             PSPC_TRY_CUDA(e);
         }
         int rc = read_status();
@@ -973,6 +999,7 @@ struct Builder {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ek0, ek1);
             kernel_ms += ms;
+            offchip_ms += ms;
         }
         return PSPC_OK;
     }
@@ -1004,6 +1031,9 @@ struct Builder {
         if (plan.smem_bytes + 1024 > (size_t)smem_optin) return PSPC_E_INVAL;  // tables must fit on chip
         PSPC_TRY_CUDA(level_kernel_attrs(plan.map_kind, plan.smem_bytes, &plan.occupancy));
         if (plan.occupancy < 1) return PSPC_E_INVAL;
+        plan.light_smem_bytes = level_layout(kLightCap, level_map_bytes(kMapSeg, d, 0, 0), kLightThreads).total;
+        PSPC_TRY_CUDA(level_kernel_attrs(kMapSeg, plan.light_smem_bytes, &plan.light_occupancy, kLightThreads));
+        if (plan.light_occupancy < 1) return PSPC_E_INVAL;
         return PSPC_OK;
     }
 
@@ -1156,10 +1186,12 @@ struct Builder {
             }
             int n_off = 0;
             kernel_ms = 0.f;
+            offchip_ms = 0.f;
             for (int attempt = 0;; ++attempt) {
                 if ((rc = run_level_kernels(d, plan, n_off))) break;
                 if (!hstt->arena_overflow) break;
                 kernel_ms = 0.f;
+                offchip_ms = 0.f;
                 if (attempt > 4) {
                     rc = PSPC_E_NOMEM;
                     break;
@@ -1174,7 +1206,7 @@ struct Builder {
                 keep.lmk_proven = 0;
                 keep.n_retry = 0;
                 keep.arena_overflow = 0;
-                keep.work_smem = keep.work_global = 0;
+                keep.work_smem = keep.work_global = keep.work_light = 0;
                 cudaMemcpyAsync(stt, &keep, sizeof(LevelStatus), cudaMemcpyHostToDevice, st);
                 *hstt = keep;
             }
@@ -1195,6 +1227,8 @@ struct Builder {
             ls.kernel_ms = kernel_ms;
             ls.landmark_pruned = (long long)hstt->lmk_pruned;
             ls.landmark_proven = (long long)hstt->lmk_proven;
+            ls.offchip_vertices = n_off;
+            ls.offchip_ms = offchip_ms;
             out.lstats.push_back(ls);
             if (o.verbose)
                 fprintf(stderr, "pspc level %d: raw %lld unique %lld entries %lld active %d (off-chip %d) %.3f ms\n",

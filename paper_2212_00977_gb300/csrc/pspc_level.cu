@@ -447,16 +447,16 @@ __device__ void prune_candidates(const Map& mp, const uint64_t* __restrict__ seg
 }
 
 // Rule 2 when fewer candidates remain to be scanned than the CTA has warps
-// (P < 16: the deep levels of high-diameter graphs, where each scan is
-// long): the warps form P' >= P groups of wpc = 16 / P' warps, group g takes
+// (P < NT/32: the deep levels of high-diameter graphs, where each scan is
+// long): the warps form P' >= P groups of wpc = (NT/32) / P' warps, group g takes
 // the g-th candidate still undecided, and its warps split levels 1..d-2
 // into wpc contiguous ranges. A warp that finds a witness sets the group's
 // flag, and the others stop at their next step. Every warp reaches the
 // barriers (the call is made by the whole CTA).
-template <class Map>
+template <int NT, class Map>
 __device__ void prune_split(const Map& mp, const uint64_t* __restrict__ seg, const uint32_t* __restrict__ hub_arena,
                             int64_t n, int d, uint32_t* list, const uint32_t* ckeys, int M, int P, int* s_flag) {
-    constexpr int kWarps = kLevelThreads / 32;
+    constexpr int kWarps = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int wpc = 1;
     while (wpc * 2 * P <= kWarps) wpc *= 2;
@@ -575,13 +575,13 @@ __device__ void prune_by_level(const Map& mp, const uint64_t* __restrict__ seg,
 // first entries of L_1(h), so reading further descriptors up front only
 // costs loads). Few candidates: wider groups over the concatenated levels,
 // so that the long scans of deep levels keep all lanes busy.
-template <class Map>
+template <int NT, class Map>
 __device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, const uint32_t* hub_arena, int64_t n,
                                           int d, uint32_t* list, const uint32_t* ckeys, int M, int to_scan,
                                           int* next, const uint64_t* useg, int* s_flag) {
     if (to_scan >= 64) prune_by_level<8>(mp, seg, hub_arena, n, d, list, ckeys, M, next, useg);
-    else if (to_scan >= 16) prune_candidates<16>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
-    else prune_split(mp, seg, hub_arena, n, d, list, ckeys, M, to_scan, s_flag);
+    else if (to_scan >= NT / 32) prune_candidates<16>(mp, seg, hub_arena, n, d, list, ckeys, M, next);
+    else prune_split<NT>(mp, seg, hub_arena, n, d, list, ckeys, M, to_scan, s_flag);
 }
 
 // Landmark filter (Section "Landmark-Based Filtering"). For a candidate h
@@ -597,13 +597,14 @@ __device__ __forceinline__ void prune_all(const Map& mp, const uint64_t* seg, co
 // per thread: every read of a round precedes its writes, and no write
 // reaches past the round's reads). Returns kept; *n_proven receives the
 // proven ones among them.
+template <int NT>
 __device__ int landmark_filter(const LevelArgs& A, const uint32_t* s_lmk, int d, uint32_t* list,
                                const uint32_t* ckeys, int M, int* s_wcnt, int* s_kept, int* n_proven) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t dd = (uint32_t)d * 0x00010001u;  // d <= 32767 in both halfwords
     const int words = A.lmk_words;
     int kept = 0, proven = 0;
-    for (int base = 0; base < M; base += kLevelThreads) {
+    for (int base = 0; base < M; base += NT) {
         const int c = base + tid;
         uint32_t slot = 0;
         bool keep = false, sure = false;
@@ -634,7 +635,7 @@ __device__ int landmark_filter(const LevelArgs& A, const uint32_t* s_lmk, int d,
         if (lane == 0) s_wcnt[warp] = __popc(bal) | (__popc(bsure) << 16);
         __syncthreads();
         int before = 0, round = 0, round_sure = 0;
-        for (int w = 0; w < kLevelThreads / 32; ++w) {
+        for (int w = 0; w < NT / 32; ++w) {
             const int v = s_wcnt[w];
             before += w < warp ? (v & 0xFFFF) : 0;
             round += v & 0xFFFF;
@@ -671,20 +672,20 @@ __device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
 // ---------------------------------------------------------------------------
 // The level kernel.
 
-template <int kMap, bool kOffChip>
-__global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
+template <int kMap, bool kOffChip, int NT>
+__global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_item, s_nkeys, s_abort, s_m, s_next, s_nsurv, s_kept;
     __shared__ uint32_t s_lmk[32];  // u's landmark distances (uint16 pairs)
     __shared__ uint64_t s_useg[kUSideLevels];  // u's level descriptors for the rule-2 scan
-    __shared__ int s_wcnt[kLevelThreads / 32];
+    __shared__ int s_wcnt[NT / 32];
     __shared__ unsigned long long s_base;
-    __shared__ long long s_wsum[kLevelThreads / 32];
+    __shared__ long long s_wsum[NT / 32];
 
     const int d = A.d;
     const int64_t n = A.n;
     const size_t map_bytes = level_map_bytes(kMap, d, A.bm_words, A.cap_u_max);
-    const LevelLayout L = level_layout(A.cap_c_max, map_bytes);
+    const LevelLayout L = level_layout(A.cap_c_max, map_bytes, NT);
     uint8_t* base = kOffChip ? A.gscratch + (size_t)blockIdx.x * A.gscratch_stride : smem;
     unsigned long long* ccnt = (unsigned long long*)(base + L.cnt);
     uint32_t* ckeys = (uint32_t*)(base + L.key);
@@ -695,7 +696,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
     long long* pfx = (long long*)(base + L.pfx);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kWarps = kLevelThreads / 32;
+    constexpr int kWarps = NT / 32;
     const uint64_t* seg_prev = A.seg + (int64_t)(d - 1) * n;
 
     for (int round = 0;; ++round) {
@@ -709,7 +710,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         const uint32_t cap_c = cand_cap_for(raw, u, A.cap_c_max);
         // Off chip the table holds every distinct hub; on chip a vertex whose
         // candidates overflow is handed to the off-chip pass.
-        const uint32_t limit = (kOffChip || cap_c < A.cap_c_max) ? cap_c : cap_c - kLevelThreads - 64;
+        const uint32_t limit = (kOffChip || cap_c < A.cap_c_max) ? cap_c : cap_c - NT - 64;
 
         BitMap bm;
         HashMap hm;
@@ -734,7 +735,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             hm.lvl = (uint16_t*)(mapr + (size_t)hm.cap * 4);
         }
 
-        for (uint32_t i = tid; i < cap_c; i += kLevelThreads) {
+        for (uint32_t i = tid; i < cap_c; i += NT) {
             ckeys[i] = kEmpty;
             ccnt[i] = 0ull;
         }
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             const uint64_t s = __ldg(A.seg + (int64_t)l * n + u);
             const uint32_t len = seg_len(s);
             const uint32_t* hs = A.hub_arena + seg_start(s);
-            for (uint32_t i = tid; i < len; i += kLevelThreads) {
+            for (uint32_t i = tid; i < len; i += NT) {
                 const uint32_t x = __ldg(hs + i) & kHubMask;
                 if (kMap == kMapBitmap) bm.insert(x, l); else hm.insert(x, l);
             }
@@ -771,13 +772,13 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             cw = cw < kSegCacheMaxWords ? cw : kSegCacheMaxWords;
             if (cw >= kSegCacheMinWords) {
                 uint32_t* cache = (uint32_t*)mapr;
-                for (uint32_t i = tid; i < (uint32_t)(d - 1) * cw; i += kLevelThreads) cache[i] = 0u;
+                for (uint32_t i = tid; i < (uint32_t)(d - 1) * cw; i += NT) cache[i] = 0u;
                 __syncthreads();
                 for (int l = 1; l < d; ++l) {
                     const uint64_t s = __ldg(A.seg + (int64_t)l * n + u);
                     const uint32_t len = seg_len(s);
                     const uint32_t* hs = A.hub_arena + seg_start(s);
-                    for (uint32_t i = tid; i < len; i += kLevelThreads) {
+                    for (uint32_t i = tid; i < len; i += NT) {
                         const uint32_t r = (__ldg(hs + i) & kHubMask) - cbase;
                         if (r >= 32u * cw) break;
                         atomicOr(&cache[(uint32_t)(l - 1) * cw + (r >> 5)], 1u << (r & 31));
@@ -797,8 +798,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         const unsigned long long* gcnt =
             push ? (const unsigned long long*)A.push_cnt : (const unsigned long long*)A.cnt_arena;
         const int64_t a0 = push ? 0 : A.rp[u], a1 = push ? 1 : A.rp[u + 1];
-        for (int64_t ca = a0; ca < a1; ca += kArcChunk) {
-            const int nc = (int)((a1 - ca) < kArcChunk ? (a1 - ca) : kArcChunk);
+        for (int64_t ca = a0; ca < a1; ca += NT) {
+            const int nc = (int)((a1 - ca) < NT ? (a1 - ca) : NT);
             if (tid < nc) {
                 if (push) {
                     const int64_t b0 = __ldg(A.push_off + A.rp[u]);
@@ -867,7 +868,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         }
 
         // candidate list
-        for (uint32_t slot = tid; slot < cap_c; slot += kLevelThreads)
+        for (uint32_t slot = tid; slot < cap_c; slot += NT)
             if (ckeys[slot] != kEmpty) list[atomicAdd(&s_m, 1)] = slot;
         __syncthreads();
         int M = s_m;
@@ -882,9 +883,9 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         if (d == 3 && (size_t)Wm * 8 <= (size_t)(L.list - L.map) && M > 0) {
             uint32_t* cand_bm = (uint32_t*)mapr;
             uint32_t* mk = cand_bm + Wm;
-            for (uint32_t i = tid; i < 2 * Wm; i += kLevelThreads) cand_bm[i] = 0u;
+            for (uint32_t i = tid; i < 2 * Wm; i += NT) cand_bm[i] = 0u;
             __syncthreads();
-            for (int c = tid; c < M; c += kLevelThreads) {
+            for (int c = tid; c < M; c += NT) {
                 const uint32_t h = (ckeys[list[c]] & kHubMask) - cbase;
                 atomicOr(&cand_bm[h >> 5], 1u << (h & 31));
             }
@@ -892,8 +893,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             const uint32_t len1 = seg_len(s1);
             const uint32_t* xs = A.hub_arena + seg_start(s1);
             __syncthreads();
-            for (uint32_t c0 = 0; c0 < len1; c0 += kArcChunk) {
-                const int nc = (int)(len1 - c0 < (uint32_t)kArcChunk ? len1 - c0 : (uint32_t)kArcChunk);
+            for (uint32_t c0 = 0; c0 < len1; c0 += NT) {
+                const int nc = (int)(len1 - c0 < (uint32_t)NT ? len1 - c0 : (uint32_t)NT);
                 if (tid < nc) {
                     const uint32_t x = __ldg(xs + c0 + tid) & kHubMask;
                     // below u's dense prefix every id is in L_<3(u), so no
@@ -944,7 +945,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                 }
                 __syncthreads();
             }
-            for (int c = tid; c < M; c += kLevelThreads) {
+            for (int c = tid; c < M; c += NT) {
                 const uint32_t slot = list[c];
                 const uint32_t h = (ckeys[slot] & kHubMask) - cbase;
                 if ((mk[h >> 5] >> (h & 31)) & 1u) list[c] = slot | kPrunedBit;
@@ -956,7 +957,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         // 3. prune rule 2 over levels 1..d-2 of each candidate's label
         int M_scan = M, n_proven = 0;
         if (d >= 3 && !marked && M > 0 && A.lmk) {
-            M_scan = landmark_filter(A, s_lmk, d, list, ckeys, M, s_wcnt, &s_kept, &n_proven);
+            M_scan = landmark_filter<NT>(A, s_lmk, d, list, ckeys, M, s_wcnt, &s_kept, &n_proven);
             if (tid == 0 && M_scan < M) atomicAdd(&A.stt->lmk_pruned, (unsigned long long)(M - M_scan));
             if (tid == 0 && n_proven) atomicAdd(&A.stt->lmk_proven, (unsigned long long)n_proven);
         }
@@ -969,10 +970,10 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             __syncthreads();
             const uint64_t* useg = useg_on ? s_useg : nullptr;
             if constexpr (kMap == kMapBitmap)
-                prune_all(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
+                prune_all<NT>(bm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
             else if constexpr (kMap == kMapHash)
-                prune_all(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
-            else prune_all(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
+                prune_all<NT>(hm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
+            else prune_all<NT>(sm, A.seg, A.hub_arena, n, d, list, ckeys, M_scan, ns, &s_next, useg, s_wcnt);
             __syncthreads();
         }
         M = M_scan;  // list[0..M) now holds every candidate that can survive
@@ -986,9 +987,9 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
         if ((size_t)W * 8 <= region) {
             uint32_t* sb = (uint32_t*)mapr;
             uint32_t* wp = sb + W;
-            for (uint32_t i = tid; i < W; i += kLevelThreads) sb[i] = 0u;
+            for (uint32_t i = tid; i < W; i += NT) sb[i] = 0u;
             __syncthreads();
-            for (int c = tid; c < M; c += kLevelThreads) {
+            for (int c = tid; c < M; c += NT) {
                 const uint32_t slot = list[c];
                 if (!(slot & kPrunedBit)) {
                     const uint32_t h = (ckeys[slot & kSlotMask] & kHubMask) - cbase;
@@ -1006,7 +1007,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                 __syncthreads();
                 const unsigned long long b0 = s_base;
                 if (b0 + S <= A.arena_cap) {
-                    for (int c = tid; c < M; c += kLevelThreads) {
+                    for (int c = tid; c < M; c += NT) {
                         const uint32_t e = list[c];
                         if (e & kPrunedBit) continue;
                         const uint32_t slot = e & kSlotMask;
@@ -1021,7 +1022,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                 }
             }
         } else {
-            for (int c = tid; c < M; c += kLevelThreads) {
+            for (int c = tid; c < M; c += NT) {
                 const uint32_t e = list[c];
                 if (!(e & kPrunedBit))
                     sortbuf[atomicAdd(&s_nsurv, 1)] =
@@ -1031,7 +1032,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
             const int S = s_nsurv;
             if (S > 0) {
                 const uint32_t P = pow2_ceil((uint64_t)S);
-                for (uint32_t i = S + tid; i < P; i += kLevelThreads) sortbuf[i] = ~0ull;
+                for (uint32_t i = S + tid; i < P; i += NT) sortbuf[i] = ~0ull;
                 __syncthreads();
                 block_bitonic_sort(sortbuf, P);
                 if (tid == 0) {
@@ -1042,7 +1043,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const LevelArgs A) {
                 __syncthreads();
                 const unsigned long long b0 = s_base;
                 if (b0 + S <= A.arena_cap) {
-                    for (int i = tid; i < S; i += kLevelThreads) {
+                    for (int i = tid; i < S; i += NT) {
                         const uint32_t slot = (uint32_t)sortbuf[i];
                         const uint32_t key = ckeys[slot];
                         A.hub_arena[b0 + i] = (key & kHubMask) | (key & kOvfBit);
@@ -1135,27 +1136,40 @@ cudaError_t launch_cost(int d, int64_t n, int64_t arcs, const int64_t* rp, const
     return cudaGetLastError();
 }
 
-cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy) {
-    const void* f = map_kind == kMapBitmap ? (const void*)k_level<kMapBitmap, false>
-                    : map_kind == kMapHash ? (const void*)k_level<kMapHash, false>
-                                           : (const void*)k_level<kMapSeg, false>;
+template <int NT>
+static const void* level_fn(int map_kind, bool offchip) {
+    if (offchip) return map_kind == kMapSeg ? (const void*)k_level<kMapSeg, true, NT> : (const void*)k_level<kMapHash, true, NT>;
+    return map_kind == kMapBitmap ? (const void*)k_level<kMapBitmap, false, NT>
+           : map_kind == kMapHash ? (const void*)k_level<kMapHash, false, NT>
+                                  : (const void*)k_level<kMapSeg, false, NT>;
+}
+
+cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy, int nt) {
+    const void* f = nt == kLightThreads ? level_fn<kLightThreads>(map_kind, false) : level_fn<kLevelThreads>(map_kind, false);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, f, kLevelThreads, smem_bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, f, nt, smem_bytes);
+}
+
+template <int NT>
+static void launch_level_nt(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,
+                            cudaStream_t st) {
+    if (offchip && map_kind == kMapSeg)
+        k_level<kMapSeg, true, NT><<<grid, NT, 0, st>>>(A);
+    else if (offchip)
+        k_level<kMapHash, true, NT><<<grid, NT, 0, st>>>(A);
+    else if (map_kind == kMapBitmap)
+        k_level<kMapBitmap, false, NT><<<grid, NT, smem_bytes, st>>>(A);
+    else if (map_kind == kMapHash)
+        k_level<kMapHash, false, NT><<<grid, NT, smem_bytes, st>>>(A);
+    else
+        k_level<kMapSeg, false, NT><<<grid, NT, smem_bytes, st>>>(A);
 }
 
 cudaError_t launch_level(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,
-                         cudaStream_t st) {
-    if (offchip && map_kind == kMapSeg)
-        k_level<kMapSeg, true><<<grid, kLevelThreads, 0, st>>>(A);
-    else if (offchip)
-        k_level<kMapHash, true><<<grid, kLevelThreads, 0, st>>>(A);
-    else if (map_kind == kMapBitmap)
-        k_level<kMapBitmap, false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
-    else if (map_kind == kMapHash)
-        k_level<kMapHash, false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
-    else
-        k_level<kMapSeg, false><<<grid, kLevelThreads, smem_bytes, st>>>(A);
+                         cudaStream_t st, int nt) {
+    if (nt == kLightThreads && !offchip) launch_level_nt<kLightThreads>(map_kind, false, grid, smem_bytes, A, st);
+    else launch_level_nt<kLevelThreads>(map_kind, offchip, grid, smem_bytes, A, st);
     return cudaGetLastError();
 }
 

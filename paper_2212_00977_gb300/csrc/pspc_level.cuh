@@ -10,8 +10,15 @@
 
 namespace pspc {
 
-constexpr int kLevelThreads = 512;
-constexpr int kArcChunk = kLevelThreads;  // arcs staged per gather chunk
+constexpr int kLevelThreads = 512;  // CTA of the level kernel for heavy vertices
+constexpr int kLightThreads = 128;  // CTA of the level kernel for light vertices
+constexpr uint32_t kLightCap = 1024;  // candidate slots of a light vertex
+constexpr int kLightBucket = 9;       // light: fewer than 2^9 pulled entries, so at most 2 * 511 < kLightCap
+                                      // slots are asked for, and the table never overflows
+constexpr int kArcChunk = kLevelThreads;  // arcs staged per gather chunk (the CTA size)
+
+// Resident CTAs per SM each kernel size is built for (64 registers a thread).
+__host__ __device__ constexpr int level_min_blocks(int nt) { return nt >= 512 ? 2 : 8; }
 constexpr int kBuckets = 64;
 constexpr size_t kBitmapBudget = 40 * 1024;  // on-chip bytes for the level bitmaps
 constexpr int kLmkShallow = 32;    // landmarks the filter tests below level kLmkDeepLevel
@@ -34,7 +41,7 @@ struct LevelStatus {
     int arena_overflow;
     int work_smem;
     int work_global;
-    int pad;
+    int work_light;
     int bucket_cnt[kBuckets];
     int bucket_base[kBuckets];
     int bucket_fill[kBuckets];
@@ -85,7 +92,7 @@ struct LevelLayout {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline LevelLayout level_layout(uint32_t cap_c, size_t map_bytes) {
+__host__ __device__ inline LevelLayout level_layout(uint32_t cap_c, size_t map_bytes, int nt = kLevelThreads) {
     LevelLayout L;
     size_t p = 0;
     L.cnt = p;
@@ -97,9 +104,9 @@ __host__ __device__ inline LevelLayout level_layout(uint32_t cap_c, size_t map_b
     L.list = p;
     p = align16(p + (size_t)cap_c * 4);
     L.st = p;
-    p = align16(p + (size_t)kArcChunk * 8);
+    p = align16(p + (size_t)nt * 8);
     L.pfx = p;
-    p = align16(p + (size_t)(kArcChunk + 1) * 8);
+    p = align16(p + (size_t)(nt + 1) * 8);
     L.total = p;
     return L;
 }
@@ -161,8 +168,8 @@ cudaError_t launch_cost(int d, int64_t n, int64_t arcs, const int64_t* rp, const
                         const int32_t* hpre, uint32_t* arc_lo, uint32_t* cnt_arc, int64_t* raw_u,
                         int64_t* lab_size, LevelStatus* stt, int64_t label_limit, int32_t* glist, int32_t* items,
                         cudaStream_t st, int64_t* launches);
-cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy);
+cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy, int nt = kLevelThreads);
 cudaError_t launch_level(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,
-                         cudaStream_t st);
+                         cudaStream_t st, int nt = kLevelThreads);
 
 }  // namespace pspc
