@@ -970,36 +970,47 @@ struct Builder {
         const int n_off = hstt->n_global + hstt->n_retry;
         n_offchip = n_off;
         if (n_off > 0) {
-            const uint32_t cc = (uint32_t)std::max<unsigned long long>(hstt->need_cap_c, 64);
+            // first pass: slabs of at most kOffSlabCap candidate slots, tables
+            // grown from kOffStartCap; vertices beyond the slab go to a second
+            // pass with slabs of the full bound
+            const uint32_t cc_full = (uint32_t)std::max<unsigned long long>(hstt->need_cap_c, 64);
             const uint32_t cu = (uint32_t)std::max<unsigned long long>(hstt->need_cap_u, 64);
             const int off_kind = plan.map_kind == kMapSeg ? kMapSeg : kMapHash;
-            const size_t stride = (level_layout(cc, level_map_bytes(off_kind, d, 0, cu)).total + 255) & ~(size_t)255;
             const size_t budget = (size_t)4 << 30;
-            int grid = (int)std::min<size_t>((size_t)n_off, std::max<size_t>(1, budget / stride));
-            // granular builds leave every SM half free for concurrent work
-            grid = std::min(grid, o.granular ? sms : sms * 2);
-            if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
-            rc = ensure_gscratch(stride * grid);
-            if (rc) return rc;
-            A.items = glist;
-            A.n_items = n_off;
-            A.work = &stt->work_global;
-            A.cap_c_max = cc;
-            A.cap_u_max = cu;
-            A.gscratch = gscratch;
-            A.gscratch_stride = stride;
-            A.granular = 0;  // off-chip scratch slabs are per persistent CTA
-            cudaEventRecord(ek0, st);
-            cudaError_t e = launch_level(off_kind, true, grid, 0, A, st);
-            cudaEventRecord(ek1, st);
-            out.launches += 1;
-            PSPC_TRY_CUDA(e);
-            rc = read_status();
-            if (rc) return rc;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ek0, ek1);
-            kernel_ms += ms;
-            offchip_ms += ms;
+            for (int pass = 0; pass < 2; ++pass) {
+                const int count = pass == 0 ? n_off : hstt->n_giant;
+                if (count == 0) break;
+                const uint32_t cc = pass == 0 ? std::min(cc_full, kOffSlabCap) : cc_full;
+                const size_t stride =
+                    (level_layout(cc, level_map_bytes(off_kind, d, 0, cu)).total + 255) & ~(size_t)255;
+                int grid = (int)std::min<size_t>((size_t)count, std::max<size_t>(1, budget / stride));
+                // granular builds leave every SM half free for concurrent work
+                grid = std::min(grid, o.granular ? sms : sms * 2);
+                if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
+                rc = ensure_gscratch(stride * grid);
+                if (rc) return rc;
+                A.items = pass == 0 ? glist : glist + n;
+                A.n_items = count;
+                A.work = pass == 0 ? &stt->work_global : &stt->work_giant;
+                A.cap_c_max = cc;
+                A.cap_u_max = cu;
+                A.off_start_cap = pass == 0 ? kOffStartCap : 0u;
+                A.giant_list = glist + n;
+                A.gscratch = gscratch;
+                A.gscratch_stride = stride;
+                A.granular = 0;  // off-chip scratch slabs are per persistent CTA
+                cudaEventRecord(ek0, st);
+                cudaError_t e = launch_level(off_kind, true, grid, 0, A, st);
+                cudaEventRecord(ek1, st);
+                out.launches += 1;
+                PSPC_TRY_CUDA(e);
+                rc = read_status();
+                if (rc) return rc;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ek0, ek1);
+                kernel_ms += ms;
+                offchip_ms += ms;
+            }
         }
         return PSPC_OK;
     }
@@ -1206,7 +1217,8 @@ struct Builder {
                 keep.lmk_proven = 0;
                 keep.n_retry = 0;
                 keep.arena_overflow = 0;
-                keep.work_smem = keep.work_global = keep.work_light = 0;
+                keep.work_smem = keep.work_global = keep.work_light = keep.work_giant = 0;
+                keep.n_giant = 0;
                 cudaMemcpyAsync(stt, &keep, sizeof(LevelStatus), cudaMemcpyHostToDevice, st);
                 *hstt = keep;
             }

@@ -707,10 +707,14 @@ __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelA
         const int64_t u = A.items[item];
         const uint32_t cbase = A.comp_base ? (uint32_t)__ldg(A.comp_base + u) : 0u;
         const int64_t raw = A.raw_u[u];
-        const uint32_t cap_c = cand_cap_for(raw, u, A.cap_c_max);
-        // Off chip the table holds every distinct hub; on chip a vertex whose
-        // candidates overflow is handed to the off-chip pass.
-        const uint32_t limit = (kOffChip || cap_c < A.cap_c_max) ? cap_c : cap_c - NT - 64;
+        // On chip a vertex whose candidates overflow the table is handed to
+        // the off-chip pass. Off chip the table starts at A.off_start_cap
+        // slots (0: the full bound) and doubles, the pull redone, whenever
+        // it fills to three quarters, up to the bound 2 min(raw, u) clipped
+        // to the slab (A.cap_c_max); a vertex that still overflows then goes
+        // to the final off-chip pass, whose slabs hold the full bound.
+        const uint32_t full_cap = cand_cap_for(raw, u, A.cap_c_max);
+        uint32_t cap_c = (kOffChip && A.off_start_cap) ? min(full_cap, A.off_start_cap) : full_cap;
 
         BitMap bm;
         HashMap hm;
@@ -739,6 +743,7 @@ __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelA
             ckeys[i] = kEmpty;
             ccnt[i] = 0ull;
         }
+        uint32_t limit = kOffChip ? cap_c - cap_c / 4 : (cap_c < A.cap_c_max ? cap_c : cap_c - NT - 64);
         if (kMap == kMapBitmap) bm.clear();
         else if (kMap == kMapHash) hm.clear();
         if (tid == 0) {
@@ -793,75 +798,96 @@ __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelA
         // 2. pull with the membership filter, merged per hub. In the push
         // paradigm the entries sent to u lie in one bucket, read as a
         // single segment.
-        const bool push = A.push_hub != nullptr;
-        const uint32_t* ghub = push ? A.push_hub : A.hub_arena;
-        const unsigned long long* gcnt =
-            push ? (const unsigned long long*)A.push_cnt : (const unsigned long long*)A.cnt_arena;
-        const int64_t a0 = push ? 0 : A.rp[u], a1 = push ? 1 : A.rp[u + 1];
-        for (int64_t ca = a0; ca < a1; ca += NT) {
-            const int nc = (int)((a1 - ca) < NT ? (a1 - ca) : NT);
-            if (tid < nc) {
-                if (push) {
-                    const int64_t b0 = __ldg(A.push_off + A.rp[u]);
-                    pfx[tid] = __ldg(A.push_off + A.rp[u + 1]) - b0;
-                    st[tid] = (uint64_t)b0;
-                } else {
-                    const uint32_t c = __ldg(A.cnt_arc + ca + tid);
-                    pfx[tid] = c;
-                    st[tid] = c ? seg_start(__ldg(seg_prev + __ldg(A.col + ca + tid))) +
-                                      (A.arc_lo ? __ldg(A.arc_lo + ca + tid) : 0u)
-                                : 0ull;
-                }
-            }
-            __syncthreads();
-            const long long total = block_excl_scan(pfx, nc, s_wsum);
-            for (long long cb = (long long)warp * 32 * kGatherUnroll; cb < total;
-                 cb += (long long)kWarps * 32 * kGatherUnroll) {
-                if (__shfl_sync(0xFFFFFFFFu, *(volatile int*)&s_abort, 0)) break;
-                int lo = 0, hi = nc;  // last arc whose first entry is <= cb
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (pfx[mid] <= cb) lo = mid; else hi = mid;
-                }
-                int j = lo;
-                uint32_t hw[kGatherUnroll];
-                uint64_t pos[kGatherUnroll];
-                bool ok[kGatherUnroll];
-#pragma unroll
-                for (int t = 0; t < kGatherUnroll; ++t) {
-                    const long long i = cb + t * 32 + lane;
-                    ok[t] = i < total;
-                    if (ok[t]) {
-                        while (pfx[j + 1] <= i) ++j;
-                        pos[t] = st[j] + (uint64_t)(i - pfx[j]);
-                        hw[t] = __ldg(ghub + pos[t]);
+        for (;;) {
+            const bool push = A.push_hub != nullptr;
+            const uint32_t* ghub = push ? A.push_hub : A.hub_arena;
+            const unsigned long long* gcnt =
+                push ? (const unsigned long long*)A.push_cnt : (const unsigned long long*)A.cnt_arena;
+            const int64_t a0 = push ? 0 : A.rp[u], a1 = push ? 1 : A.rp[u + 1];
+            for (int64_t ca = a0; ca < a1; ca += NT) {
+                const int nc = (int)((a1 - ca) < NT ? (a1 - ca) : NT);
+                if (tid < nc) {
+                    if (push) {
+                        const int64_t b0 = __ldg(A.push_off + A.rp[u]);
+                        pfx[tid] = __ldg(A.push_off + A.rp[u + 1]) - b0;
+                        st[tid] = (uint64_t)b0;
+                    } else {
+                        const uint32_t c = __ldg(A.cnt_arc + ca + tid);
+                        pfx[tid] = c;
+                        st[tid] = c ? seg_start(__ldg(seg_prev + __ldg(A.col + ca + tid))) +
+                                          (A.arc_lo ? __ldg(A.arc_lo + ca + tid) : 0u)
+                                    : 0ull;
                     }
                 }
-#pragma unroll
-                for (int t = 0; t < kGatherUnroll; ++t)
-                    if (ok[t]) {
-                        const uint32_t h = hw[t] & kHubMask;
-                        ok[t] = !(kMap == kMapBitmap ? bm.member(h) : kMap == kMapHash ? hm.member(h) : sm.member(h));
+                __syncthreads();
+                const long long total = block_excl_scan(pfx, nc, s_wsum);
+                for (long long cb = (long long)warp * 32 * kGatherUnroll; cb < total;
+                     cb += (long long)kWarps * 32 * kGatherUnroll) {
+                    if (__shfl_sync(0xFFFFFFFFu, *(volatile int*)&s_abort, 0)) break;
+                    int lo = 0, hi = nc;  // last arc whose first entry is <= cb
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pfx[mid] <= cb) lo = mid; else hi = mid;
                     }
-                uint64_t cv[kGatherUnroll];
-#pragma unroll
-                for (int t = 0; t < kGatherUnroll; ++t)
-                    if (ok[t]) cv[t] = __ldg(gcnt + pos[t]);
-#pragma unroll
-                for (int t = 0; t < kGatherUnroll; ++t)
-                    if (ok[t]) cand_insert(ckeys, ccnt, cap_c, limit, hw[t] & kHubMask, cv[t], hw[t] >> 31, &s_nkeys,
-                                           &s_abort);
+                    int j = lo;
+                    uint32_t hw[kGatherUnroll];
+                    uint64_t pos[kGatherUnroll];
+                    bool ok[kGatherUnroll];
+    #pragma unroll
+                    for (int t = 0; t < kGatherUnroll; ++t) {
+                        const long long i = cb + t * 32 + lane;
+                        ok[t] = i < total;
+                        if (ok[t]) {
+                            while (pfx[j + 1] <= i) ++j;
+                            pos[t] = st[j] + (uint64_t)(i - pfx[j]);
+                            hw[t] = __ldg(ghub + pos[t]);
+                        }
+                    }
+    #pragma unroll
+                    for (int t = 0; t < kGatherUnroll; ++t)
+                        if (ok[t]) {
+                            const uint32_t h = hw[t] & kHubMask;
+                            ok[t] = !(kMap == kMapBitmap ? bm.member(h) : kMap == kMapHash ? hm.member(h) : sm.member(h));
+                        }
+                    uint64_t cv[kGatherUnroll];
+    #pragma unroll
+                    for (int t = 0; t < kGatherUnroll; ++t)
+                        if (ok[t]) cv[t] = __ldg(gcnt + pos[t]);
+    #pragma unroll
+                    for (int t = 0; t < kGatherUnroll; ++t)
+                        if (ok[t]) cand_insert(ckeys, ccnt, cap_c, limit, hw[t] & kHubMask, cv[t], hw[t] >> 31, &s_nkeys,
+                                               &s_abort);
+                }
+                __syncthreads();
+                if (s_abort) break;
             }
             __syncthreads();
-            if (s_abort) break;
+            if (!kOffChip || !s_abort || cap_c >= full_cap) break;
+            // off chip: a larger table, and the pull again
+            cap_c = min(2 * cap_c, full_cap);
+            limit = cap_c - cap_c / 4;
+            for (uint32_t i = tid; i < cap_c; i += NT) {
+                ckeys[i] = kEmpty;
+                ccnt[i] = 0ull;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_nkeys = 0;
+                s_abort = 0;
+            }
+            __syncthreads();
         }
         __syncthreads();
         if (s_abort) {
             if (tid == 0) {
-                const int p = atomicAdd(&A.stt->n_retry, 1);
-                A.retry_list[p] = (int32_t)u;
-                atomicMax(&A.stt->need_cap_c, (unsigned long long)cand_cap_for(raw, u, 1u << 30));
-                atomicMax(&A.stt->need_cap_u, (unsigned long long)label_cap_for(A.lab_size[u]));
+                if (kOffChip) {
+                    A.giant_list[atomicAdd(&A.stt->n_giant, 1)] = (int32_t)u;
+                } else {
+                    const int p = atomicAdd(&A.stt->n_retry, 1);
+                    A.retry_list[p] = (int32_t)u;
+                    atomicMax(&A.stt->need_cap_c, (unsigned long long)cand_cap_for(raw, u, 1u << 30));
+                    atomicMax(&A.stt->need_cap_u, (unsigned long long)label_cap_for(A.lab_size[u]));
+                }
             }
             __syncthreads();
             continue;

@@ -13,6 +13,8 @@ namespace pspc {
 constexpr int kLevelThreads = 512;  // CTA of the level kernel for heavy vertices
 constexpr int kLightThreads = 128;  // CTA of the level kernel for light vertices
 constexpr uint32_t kLightCap = 1024;  // candidate slots of a light vertex
+constexpr uint32_t kOffStartCap = 16384;    // first off-chip table size
+constexpr uint32_t kOffSlabCap = 1u << 17;  // off-chip slab of the first pass, in candidate slots
 constexpr int kLightBucket = 9;       // light: fewer than 2^9 pulled entries, so at most 2 * 511 < kLightCap
                                       // slots are asked for, and the table never overflows
 constexpr int kArcChunk = kLevelThreads;  // arcs staged per gather chunk (the CTA size)
@@ -42,6 +44,9 @@ struct LevelStatus {
     int work_smem;
     int work_global;
     int work_light;
+    int n_giant;     // off-chip vertices whose candidates overflow the slab
+    int work_giant;
+    int pad;
     int bucket_cnt[kBuckets];
     int bucket_base[kBuckets];
     int bucket_fill[kBuckets];
@@ -72,6 +77,8 @@ struct LevelArgs {
     int* work;
     LevelStatus* stt;
     int32_t* retry_list;  // appended at retry_list[k]
+    int32_t* giant_list;  // off chip: vertices for the final pass with full-size slabs
+    uint32_t off_start_cap;  // off chip: first table size (0: the full bound)
     uint32_t cap_c_max;   // candidate table slots (on chip, or per-CTA scratch)
     uint32_t cap_u_max;   // label hash slots (hash map kind)
     uint32_t bm_words;    // words per level bitmap (bitmap map kind)
