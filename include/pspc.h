@@ -291,7 +291,7 @@ int pspc_level_stats(const pspc_index* ix, pspc_level_stat_t* out, int32_t cap,
  * sorted by source, L(s) held in an on-chip hash for every pair of that
  * source and each pair streams only L(t) (used when the call groups its
  * pairs by source, q >= 4096 and q >= n/4, and the largest label has at
- * most 8192 entries; otherwise 0 applies); 0 = PSPC_QUERY_BY_SOURCE when
+ * most 12,287 entries; otherwise 0 applies); 0 = PSPC_QUERY_BY_SOURCE when
  * it applies and q >= 64 n, else chosen from the average label size.
  * Results do not depend on it. Errors: PSPC_E_INVAL.
  */

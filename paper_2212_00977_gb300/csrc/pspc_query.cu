@@ -298,17 +298,24 @@ __global__ void __launch_bounds__(kQueryThreads, 6) k_query_chunked(const QueryA
 // The sorted pairs are cut into items of kBySourceItem; a CTA takes items
 // in turn and walks each item's runs of pairs with one source s. For a run
 // it puts L(s) into an on-chip hash (slot = hub | distance << 24 | entry
-// index << 40), then each warp answers one pair of the run at a time by
-// streaming L(t), kBySourceUnroll loads in flight per lane, and probing the
-// hash for each hub. L(s) is read once per run instead of once per pair,
-// and no warp waits on a second list. The table has pow2 >= 2|L(s)| slots
-// (at most max_slots, which the host sizes from the largest label), so a
-// probe always ends at an empty slot.
-constexpr int kBySourceItem = 128;
+// index << 40), then each of its warps answers one pair of the run at a
+// time by streaming L(t), kBySourceUnroll loads in flight per lane, and
+// probing the hash for each hub. L(s) is read once per run instead of once
+// per pair, and no warp waits on a second list. The table has a power of
+// two >= 4/3 |L(s)| slots (at most max_slots, which the host sizes from the
+// largest label), so it is at most three quarters full and a probe always
+// ends at an empty slot.
+constexpr int kBySourceItem = 512;
+constexpr int kBySourceThreads = 1024;  // CTA size with large tables (one CTA per SM); 256 with small ones
 constexpr int kBySourceUnroll = 8;
 constexpr unsigned long long kEmptySlot = ~0ull;
 
-__global__ void __launch_bounds__(kQueryThreads) k_query_by_source(const QueryArgs Q, uint32_t max_slots) {
+__host__ __device__ inline uint32_t by_source_table(uint64_t label) {
+    const uint32_t s = pow2_ceil(label + label / 3 + 1);
+    return s < 64u ? 64u : s;
+}
+
+__global__ void __launch_bounds__(kBySourceThreads) k_query_by_source(const QueryArgs Q, uint32_t max_slots) {
     extern __shared__ unsigned long long tab[];
     __shared__ int32_t s_src[kBySourceItem];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -316,7 +323,7 @@ __global__ void __launch_bounds__(kQueryThreads) k_query_by_source(const QueryAr
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int64_t kb = item * kBySourceItem;
         const int m = (int)(Q.q - kb < kBySourceItem ? Q.q - kb : kBySourceItem);
-        if (tid < m) s_src[tid] = __ldg(Q.pairs + 2 * (int64_t)__ldg(Q.perm + kb + tid));
+        for (int i = tid; i < m; i += blockDim.x) s_src[i] = __ldg(Q.pairs + 2 * (int64_t)__ldg(Q.perm + kb + i));
         __syncthreads();
         for (int r0 = 0; r0 < m;) {
             const int32_t s = s_src[r0];
@@ -334,8 +341,8 @@ __global__ void __launch_bounds__(kQueryThreads) k_query_by_source(const QueryAr
             const int32_t rs = __ldg(Q.rank + s);
             const int64_t a0 = __ldg(Q.off + rs);
             const uint32_t la = (uint32_t)(__ldg(Q.off + rs + 1) - a0);
-            uint32_t slots = pow2_ceil(2ull * la);
-            slots = slots < 64u ? 64u : (slots > max_slots ? max_slots : slots);
+            uint32_t slots = by_source_table(la);
+            slots = slots > max_slots ? max_slots : slots;
             const uint32_t mask = slots - 1;
             for (uint32_t i = tid; i < slots; i += blockDim.x) tab[i] = kEmptySlot;
             __syncthreads();
@@ -350,7 +357,7 @@ __global__ void __launch_bounds__(kQueryThreads) k_query_by_source(const QueryAr
                 }
             }
             __syncthreads();
-            for (int r = r0 + w; r < r1; r += kChunkWarps) {
+            for (int r = r0 + w; r < r1; r += (int)(blockDim.x >> 5)) {
                 const int64_t p = __ldg(Q.perm + kb + r);
                 const int32_t t = __ldg(Q.pairs + 2 * p + 1);
                 if (t < 0 || t >= Q.n) {
@@ -464,8 +471,8 @@ static void set_query_carveouts() {
 // Table slots the by-source kernel needs for the largest label (0: it does
 // not fit on chip).
 static uint32_t by_source_slots(const Index& ix) {
-    const uint32_t s = pow2_ceil(2ull * (uint64_t)(ix.max_label > 0 ? ix.max_label : 1));
-    return s <= kBySourceMaxSlots ? (s < 64u ? 64u : s) : 0u;
+    const uint32_t s = by_source_table((uint64_t)(ix.max_label > 0 ? ix.max_label : 1));
+    return s <= kBySourceMaxSlots ? s : 0u;
 }
 
 // The query kernel. Automatic choice: by source when the pairs are grouped,
@@ -502,11 +509,14 @@ static cudaError_t launch_query(Index& ix, const QueryArgs& Q, cudaStream_t st) 
     if (G == PSPC_QUERY_BY_SOURCE) {
         const uint32_t slots = by_source_slots(ix);
         const size_t smem = (size_t)slots * 8;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_query_by_source, kQueryThreads, smem);
+        // tables above a quarter of the shared memory leave room for one CTA
+        // per SM: make it a large one; smaller tables share SMs
+        const int threads = smem > (size_t)56 * 1024 ? kBySourceThreads : kQueryThreads;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_query_by_source, threads, smem);
         if (e != cudaSuccess) return e;
         const int64_t items = (Q.q + kBySourceItem - 1) / kBySourceItem;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * std::max(occ, 1)));
-        k_query_by_source<<<grid, kQueryThreads, smem, st>>>(Q, slots);
+        k_query_by_source<<<grid, threads, smem, st>>>(Q, slots);
         return cudaGetLastError();
     }
     const void* fn = G == 8 ? (const void*)k_query<8>
