@@ -682,6 +682,7 @@ def run_serve(args):
                 off += sz
 
     done_builds = 0
+    failed_builds = []
     stop_reaper = threading.Event()
 
     def reaper():
@@ -697,8 +698,8 @@ def run_serve(args):
                 r.wait(600)
                 done_builds += 1
                 srv.drop_index(name)
-            except MemoryError:
-                pass
+            except Exception as e:  # reported, not fatal to the load
+                failed_builds.append(repr(e))
             k += 1
 
     th = threading.Thread(target=driver)
@@ -711,6 +712,7 @@ def run_serve(args):
     stop_reaper.set()
     rp.join()
     t_end = max(r.finished for r in reqs_q)
+    sst = srv.stats()
     srv.close()
     lat_ms = [1e3 * r.latency for r in reqs_q]
     blat_ms = [1e3 * r.latency for _, r in reqs_b if r.finished]
@@ -725,7 +727,9 @@ def run_serve(args):
                        "requests": len(arrivals), "query_requests": len(reqs_q), "build_requests": len(reqs_b)},
             "p50_ms": serve.percentile(lat_ms, 50), "p99_ms": serve.percentile(lat_ms, 99),
             "p50_build_ms": serve.percentile(blat_ms, 50), "p99_build_ms": serve.percentile(blat_ms, 99),
-            "builds_done": done_builds, "batches": srv.batches, "pairs": pairs_total}
+            "builds_done": done_builds, "batches": srv.batches, "pairs": pairs_total,
+            "requests_per_batch": sst["requests_per_batch"], "pairs_per_batch": pairs_total / max(sst["batches"], 1),
+            "max_builds_running": sst["max_builds_running"], "builds_failed": failed_builds}
     print(json.dumps(line), flush=True)
     return 0
 

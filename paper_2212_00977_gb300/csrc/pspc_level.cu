@@ -1170,9 +1170,20 @@ static const void* level_fn(int map_kind, bool offchip) {
                                   : (const void*)k_level<kMapSeg, false, NT>;
 }
 
+// The kernel's dynamic shared-memory limit is raised to the device's
+// opt-in maximum, the same value on every call: builds that run at the same
+// time on other threads never see it lowered under a launch.
 cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy, int nt) {
     const void* f = nt == kLightThreads ? level_fn<kLightThreads>(map_kind, false) : level_fn<kLevelThreads>(map_kind, false);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    const size_t max_dyn = (size_t)optin - fa.sharedSizeBytes;
+    if (smem_bytes > max_dyn) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dyn);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, f, nt, smem_bytes);
 }

@@ -1,5 +1,7 @@
 """Serving: continuously batched queries and overlapping builds give every
-request exactly the answer the oracle gives, and the answer it gets alone."""
+request exactly the answer the oracle gives, and the answer it gets alone;
+builds are admitted by their estimated memory, wait for it when it is taken,
+and fail at once only when they could never fit."""
 from __future__ import annotations
 
 import threading
@@ -82,8 +84,60 @@ def test_results_same_alone_and_in_the_mix(env):
             rd, rc, rf = alone[name].query(pairs)
             assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf)
         assert srv.batches < len(reqs)  # requests were batched
+        assert srv.stats()["requests_per_batch"] > 1
         lat = [r.latency for _, _, r in reqs]
         assert serve.percentile(lat, 99) < 60
+    finally:
+        srv.close()
+
+
+def test_build_waits_for_memory_then_runs(env):
+    """A build whose estimate fits the budget, but not next to a resident
+    index, waits (it neither fails nor starts) until that index is dropped,
+    then runs; its answers equal the oracle's. Two builds that fit together
+    run at the same time."""
+    torch, pspc, serve = env
+    ga, ra, _ = P.workload("ba2000")
+    gb = P.barabasi_albert(3000, 3, 21)
+    rb = G.degree_rank(gb)
+    A = pspc.Index.from_graph(ga, ra)
+    a_bytes = A.stats()["index_bytes"]
+    need_b = serve.estimate_index_bytes(gb.n, gb.arcs)
+    srv = serve.SPCServer(max_batch_pairs=1 << 13, memory_budget=a_bytes + need_b - 1)
+    try:
+        srv.add_index("A", A)
+        rb_req = srv.submit_build("B", gb, rb)
+        time.sleep(1.0)
+        assert not rb_req.done.is_set() and rb_req.started is None  # waiting for memory
+        # queries keep being served meanwhile
+        d, c, f = srv.submit_query("A", np.array([[0, 1], [5, 7]], np.int32)).wait(60)
+        od, oc, of, _ = oracle.OracleIndex(ga, ra).query(np.array([[0, 1], [5, 7]], np.int32))
+        assert np.array_equal(d, od) and np.array_equal(c, oc)
+        t_drop = time.perf_counter()
+        srv.drop_index("A")
+        rb_req.wait(120)
+        assert rb_req.started >= t_drop
+        pairs = np.random.default_rng(3).integers(0, gb.n, size=(5000, 2)).astype(np.int32)
+        d, c, f = srv.submit_query("B", pairs).wait(60)
+        od, oc, of, _ = oracle.OracleIndex(gb, rb).query(pairs)
+        assert np.array_equal(d, od) and np.array_equal(c, oc) and np.array_equal(f, of)
+    finally:
+        srv.close()
+    # two builds admitted together overlap
+    srv = serve.SPCServer(max_batch_pairs=1 << 13, max_builds=2)
+    try:
+        g1, g2 = G.grid(60), G.grid(61)
+        r1 = srv.submit_build("g1", g1, G.random_rank(g1.n, 1))
+        r2 = srv.submit_build("g2", g2, G.random_rank(g2.n, 2))
+        r1.wait(120)
+        r2.wait(120)
+        assert max(r1.started, r2.started) < min(r1.finished, r2.finished)
+        assert srv.stats()["max_builds_running"] == 2
+        for name, g, rk in (("g1", g1, G.random_rank(g1.n, 1)), ("g2", g2, G.random_rank(g2.n, 2))):
+            pairs = np.random.default_rng(4).integers(0, g.n, size=(3000, 2)).astype(np.int32)
+            d, c, f = srv.submit_query(name, pairs).wait(60)
+            od, oc, of, _ = oracle.OracleIndex(g, rk).query(pairs)
+            assert np.array_equal(d, od) and np.array_equal(c, oc) and np.array_equal(f, of)
     finally:
         srv.close()
 
@@ -100,3 +154,31 @@ def test_admission_rejects_a_build_that_cannot_fit(env):
             srv.submit_query("nope", np.array([[0, 1]], np.int32)).wait(60)
     finally:
         srv.close()
+
+
+def test_concurrent_builds_from_threads(env):
+    """Builds of different graphs (different on-chip table plans) run at the
+    same time from two threads on their own streams; every one succeeds and
+    equals the oracle."""
+    torch, pspc, serve = env
+    graphs = [P.barabasi_albert(int(n), int(m), 40 + i) for i, (n, m) in
+              enumerate(zip(np.linspace(600, 9000, 16), [2, 3, 4, 5, 6, 7, 8, 3] * 2))]
+    ranks = [G.degree_rank(g) for g in graphs]
+    results = [None] * len(graphs)
+
+    def worker(idx):
+        st = torch.cuda.Stream()
+        for i in idx:
+            ix = pspc.Index.from_graph(graphs[i], ranks[i], stream=st)
+            results[i] = ix.export()
+            ix.free()
+
+    ts = [threading.Thread(target=worker, args=(list(range(j, len(graphs), 2)),)) for j in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for g, rk, got in zip(graphs, ranks, results):
+        ref = oracle.OracleIndex(g, rk).export()
+        for a, b in zip(got, (ref.off, ref.hub, ref.dist, ref.cnt, ref.ovf)):
+            assert np.array_equal(a, b)
