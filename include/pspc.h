@@ -119,6 +119,13 @@ typedef struct {
                                 from its bucket. Same index; the buckets
                                 hold a level's pulled entries (12 bytes
                                 each), PSPC_E_NOMEM when they do not fit */
+    int32_t warp_levels;     /* vertices with fewer than 64 pulled entries
+                                run one warp per vertex (no CTA barrier) at
+                                levels 2..warp_levels, and in 128-thread
+                                CTAs above; 0 = automatic (levels 2 and 3,
+                                and up to level 127 while the previous
+                                level had under 32 candidates per active
+                                vertex), -1 = never. Same results */
 } pspc_opts;
 
 /* Per-level counters of the last build (level d = distance d). */

@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
                 ("arena_entries", ctypes.c_int64), ("max_levels", ctypes.c_int32),
                 ("verbose", ctypes.c_int32), ("map_kind", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
                 ("granular", ctypes.c_int32), ("landmarks", ctypes.c_int32), ("reduce_shell", ctypes.c_int32),
-                ("paradigm", ctypes.c_int32)]
+                ("paradigm", ctypes.c_int32), ("warp_levels", ctypes.c_int32)]
 
 
 class GraphDesc(ctypes.Structure):
@@ -174,7 +174,7 @@ class Index:
     @classmethod
     def build(cls, n: int, row_ptr, col, rank, *, stream=None, cand_capacity=0, label_capacity=0,
               arena_entries=0, max_levels=0, verbose=False, map_kind=0, max_ctas=0,
-              granular=False, landmarks=0, reduce_shell=False, paradigm=0) -> "Index":
+              granular=False, landmarks=0, reduce_shell=False, paradigm=0, warp_levels=0) -> "Index":
         """pspc_build over a symmetric CSR (rows strictly ascending) and a
         rank permutation (0 = highest). ``reduce_shell`` builds on the
         2-core and answers peeled tree vertices through their roots;
@@ -186,7 +186,7 @@ class Index:
         g = Csr(int(n), _ptr(row_ptr), _ptr(col))
         o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
                  int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)), int(landmarks),
-                 int(bool(reduce_shell)), int(paradigm))
+                 int(bool(reduce_shell)), int(paradigm), int(warp_levels))
         h = _P()
         rc = lib.pspc_build(ctypes.byref(g), _ptr(rank), ctypes.byref(o), ctypes.byref(h),
                             _stream_handle(stream))
@@ -197,7 +197,7 @@ class Index:
     @classmethod
     def build_batch(cls, graphs, *, stream=None, cand_capacity=0, label_capacity=0, arena_entries=0,
                     max_levels=0, verbose=False, map_kind=0, max_ctas=0,
-                    granular=False, landmarks=0) -> "Index":
+                    granular=False, landmarks=0, warp_levels=0) -> "Index":
         """pspc_build_batch over ``graphs`` = [(n, row_ptr, col, rank), ...]:
         one index over their disjoint union (graph g's vertex v has id
         base_g + v, base_g = sum of earlier n)."""
@@ -212,7 +212,8 @@ class Index:
             keep.append((rp, col, rank))
             arr[i] = GraphDesc(int(n), _ptr(rp), _ptr(col), _ptr(rank))
         o = Opts(int(cand_capacity), int(label_capacity), int(arena_entries), int(max_levels),
-                 int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)), int(landmarks))
+                 int(bool(verbose)), int(map_kind), int(max_ctas), int(bool(granular)), int(landmarks),
+                 0, 0, int(warp_levels))
         h = _P()
         rc = lib.pspc_build_batch(ctypes.cast(arr, ctypes.c_void_p), k, ctypes.byref(o), ctypes.byref(h),
                                   _stream_handle(stream))

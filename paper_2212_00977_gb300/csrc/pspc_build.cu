@@ -521,6 +521,7 @@ struct LevelPlan {
     int occupancy = 0;
     size_t light_smem_bytes = 0;  // light vertices: kLightThreads CTAs, segment-search map
     int light_occupancy = 0;
+    int micro_occupancy = 0;      // tiny vertices: the warp-per-vertex kernel
 };
 
 struct Builder {
@@ -925,9 +926,20 @@ struct Builder {
             // 2^kLightBucket pulled entries) run in small CTAs with small
             // tables and the segment-search map, so that many of them share
             // an SM; the others in full-size CTAs.
-            int n_light = 0;
-            for (int b = 0; b < kLightBucket; ++b) n_light += hstt->bucket_cnt[b];
-            const int n_heavy = hstt->n_smem - n_light;
+            int n_light = 0, n_micro = 0;
+            // Automatic: one warp per tiny vertex at levels 2 and 3, and
+            // deeper (up to level 127) while the last level had few
+            // candidates per vertex: there the warp's own rule-2 scans are
+            // short or rare.
+            bool warp_level = o.warp_levels > 0 && d <= o.warp_levels;
+            if (o.warp_levels == 0 && !out.lstats.empty()) {
+                const pspc_level_stat_t& pl = out.lstats.back();
+                warp_level = d <= 3 || (d <= kWarpLevelsMax && pl.active_vertices > 0 &&
+                                        pl.unique_candidates < kWarpLevelsFew * pl.active_vertices);
+            }
+            for (int b = 0; b < kLightBucket; ++b)
+                (warp_level && b < kMicroBucket ? n_micro : n_light) += hstt->bucket_cnt[b];
+            const int n_heavy = hstt->n_smem - n_light - n_micro;
             A.granular = o.granular ? 1 : 0;
             cudaEventRecord(ek0, st);
             cudaError_t e = cudaSuccess;
@@ -955,6 +967,17 @@ struct Builder {
                 if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
                 if (o.granular) grid = n_light;
                 e = launch_level(kMapSeg, false, grid, plan.light_smem_bytes, A, st, kLightThreads);
+                out.launches += 1;
+            }
+            if (e == cudaSuccess && n_micro > 0) {  // one warp per vertex
+                A.items = items + n_heavy + n_light;
+                A.n_items = n_micro;
+                A.work = &stt->work_micro;
+                const int per_cta = kMicroThreads / 32;
+                int grid = (n_micro + per_cta - 1) / per_cta;
+                if (!o.granular) grid = std::min(grid, sms * plan.micro_occupancy);
+                if (o.max_ctas > 0 && !o.granular) grid = std::min(grid, o.max_ctas);
+                e = launch_level_micro(grid, A, st);
                 out.launches += 1;
             }
             cudaEventRecord(ek1, st);
@@ -1045,6 +1068,8 @@ struct Builder {
         plan.light_smem_bytes = level_layout(kLightCap, level_map_bytes(kMapSeg, d, 0, 0), kLightThreads).total;
         PSPC_TRY_CUDA(level_kernel_attrs(kMapSeg, plan.light_smem_bytes, &plan.light_occupancy, kLightThreads));
         if (plan.light_occupancy < 1) return PSPC_E_INVAL;
+        PSPC_TRY_CUDA(micro_kernel_occupancy(&plan.micro_occupancy));
+        if (plan.micro_occupancy < 1) return PSPC_E_INVAL;
         return PSPC_OK;
     }
 
@@ -1217,7 +1242,7 @@ struct Builder {
                 keep.lmk_proven = 0;
                 keep.n_retry = 0;
                 keep.arena_overflow = 0;
-                keep.work_smem = keep.work_global = keep.work_light = keep.work_giant = 0;
+                keep.work_smem = keep.work_global = keep.work_light = keep.work_giant = keep.work_micro = 0;
                 keep.n_giant = 0;
                 cudaMemcpyAsync(stt, &keep, sizeof(LevelStatus), cudaMemcpyHostToDevice, st);
                 *hstt = keep;
@@ -1373,7 +1398,7 @@ static void fill_defaults(pspc_opts& o, const pspc_opts* user) {
 
 static bool opts_ok(const pspc_opts& o) {
     return o.map_kind >= 0 && o.map_kind <= 3 && o.max_ctas >= 0 && (o.granular == 0 || o.granular == 1) &&
-           o.landmarks >= -1 && o.landmarks <= 64 && (o.paradigm == 0 || o.paradigm == 1);
+           o.landmarks >= -1 && o.landmarks <= 64 && (o.paradigm == 0 || o.paradigm == 1) && o.warp_levels >= -1;
 }
 
 static bool pow2_in(int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }

@@ -1085,6 +1085,257 @@ __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelA
 }
 
 // ---------------------------------------------------------------------------
+// The level for tiny vertices (fewer than 2^kMicroBucket pulled entries):
+// one warp per vertex and no CTA barrier, so that many such vertices (the
+// deep levels of high-diameter graphs, the tails of power-law graphs) are in
+// flight per SM. The warp stages the pulled entries on chip, drops those
+// whose hub is already in L_<d(u) (segment search), sorts the rest by hub
+// (a 64-element bitonic sort in registers, two elements per lane) and sums
+// the counts of equal hubs with a segmented scan (mod 2^64; the flag takes
+// the entries' flags and every carry: Label Merging). Rule 2 then runs per
+// candidate: the landmark filter, and for the undecided ones a scan of
+// levels 1..d-2 of L(h) by the whole warp. Survivors are already in hub
+// order and are appended as L_d(u).
+constexpr int kMicroWarps = kMicroThreads / 32;
+
+__device__ __forceinline__ void add_count(uint64_t& sum, uint32_t& flag, uint64_t c, uint32_t f) {
+    const uint64_t s = sum + c;
+    flag |= f | (uint32_t)(s < c);
+    sum = s;
+}
+
+__global__ void __launch_bounds__(kMicroThreads) k_level_micro(const LevelArgs A) {
+    __shared__ uint32_t s_hub[kMicroWarps][64];
+    __shared__ unsigned long long s_cnt[kMicroWarps][64];
+    __shared__ uint32_t s_lmkw[kMicroWarps][32];
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int d = A.d;
+    const int64_t n = A.n;
+    const uint64_t* seg_prev = A.seg + (int64_t)(d - 1) * n;
+    uint32_t* hb = s_hub[w];
+    unsigned long long* cbuf = s_cnt[w];
+    uint32_t* ul = s_lmkw[w];
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long n_uniq = 0, n_lpr = 0, n_lpv = 0;
+    for (int round = 0;; ++round) {
+        int item;
+        if (A.granular) {
+            item = round == 0 ? (int)(blockIdx.x * kMicroWarps + w) : A.n_items;
+        } else {
+            item = 0;
+            if (lane == 0) item = atomicAdd(A.work, 1);
+            item = __shfl_sync(FULL, item, 0);
+        }
+        if (item >= A.n_items) break;
+        const int64_t u = A.items[item];
+        SegMap sm;
+        sm.seg = A.seg;
+        sm.hub_arena = A.hub_arena;
+        sm.n = n;
+        sm.u = u;
+        sm.d = d;
+        sm.cache = nullptr;
+        sm.cwords = 0;
+        sm.base = 0;
+
+        // 1. stage the pulled entries (fewer than 64)
+        int total = 0;
+        if (A.push_hub) {
+            const int64_t b0 = __ldg(A.push_off + A.rp[u]);
+            total = (int)(__ldg(A.push_off + A.rp[u + 1]) - b0);
+            for (int i = lane; i < total; i += 32) {
+                hb[i] = __ldg(A.push_hub + b0 + i);
+                cbuf[i] = __ldg((const unsigned long long*)A.push_cnt + b0 + i);
+            }
+        } else {
+            const int64_t a0 = A.rp[u], a1 = A.rp[u + 1];
+            for (int64_t ca = a0; ca < a1; ca += 32) {
+                const int64_t a = ca + lane;
+                uint32_t c = 0;
+                uint64_t st = 0;
+                if (a < a1) {
+                    c = __ldg(A.cnt_arc + a);
+                    if (c) st = seg_start(__ldg(seg_prev + __ldg(A.col + a))) + (A.arc_lo ? __ldg(A.arc_lo + a) : 0u);
+                }
+                uint32_t incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int base = total + (int)(incl - c);
+                for (uint32_t i = 0; i < c; ++i) {
+                    hb[base + i] = __ldg(A.hub_arena + st + i);
+                    cbuf[base + i] = __ldg((const unsigned long long*)A.cnt_arena + st + i);
+                }
+                total += (int)__shfl_sync(FULL, incl, 31);
+            }
+        }
+        __syncwarp();
+
+        // 2. membership filter and sort keys: hub << 6 | entry, 0xFFFFFFFF
+        // for dropped and absent entries (they sort last)
+        uint32_t key[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int e = lane + 32 * j;
+            key[j] = 0xFFFFFFFFu;
+            if (e < total) {
+                const uint32_t h = hb[e] & kHubMask;
+                if (!sm.member(h)) key[j] = (h << 6) | (uint32_t)e;
+            }
+        }
+#pragma unroll
+        for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                if (jj == 32) {  // partners in the same lane
+                    const bool asc = (lane & k) == 0;
+                    const uint32_t lo = min(key[0], key[1]), hi = max(key[0], key[1]);
+                    key[0] = asc ? lo : hi;
+                    key[1] = asc ? hi : lo;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int e = lane + 32 * j;
+                        const uint32_t other = __shfl_xor_sync(FULL, key[j], jj);
+                        const bool lower = (e & jj) == 0, asc = (e & k) == 0;
+                        key[j] = (lower == asc) ? min(key[j], other) : max(key[j], other);
+                    }
+                }
+            }
+        }
+
+        // 3. segmented sums over runs of equal hubs, in sorted order
+        uint32_t hub[2], flg[2];
+        uint64_t sum[2];
+        bool valid[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            valid[j] = key[j] != 0xFFFFFFFFu;
+            hub[j] = valid[j] ? key[j] >> 6 : 0xFFFFFFFFu;
+            const int src = (int)(key[j] & 63u);
+            sum[j] = valid[j] ? (uint64_t)cbuf[src] : 0ull;
+            flg[j] = valid[j] ? (hb[src] >> 31) : 0u;
+        }
+        // a run starts where the previous element (in sorted order) has
+        // another hub; row 1's lane 0 follows row 0's lane 31
+        const uint32_t prev0 = __shfl_up_sync(FULL, hub[0], 1);
+        const uint32_t last0 = __shfl_sync(FULL, hub[0], 31);
+        const uint32_t prev1 = __shfl_up_sync(FULL, hub[1], 1);
+        const bool head0 = valid[0] && (lane == 0 || prev0 != hub[0]);
+        const bool head1 = valid[1] && (lane == 0 ? last0 != hub[1] : prev1 != hub[1]);
+        const unsigned h0 = __ballot_sync(FULL, head0), h1 = __ballot_sync(FULL, head1);
+        const int id0 = __popc(h0 & (lt | (1u << lane)));                       // segment id (1-based)
+        const int id1 = __popc(h0) + __popc(h1 & (lt | (1u << lane)));
+        int id[2] = {id0, id1};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t sv = __shfl_up_sync(FULL, sum[j], o);
+                const uint32_t fv = __shfl_up_sync(FULL, flg[j], o);
+                const int iv = __shfl_up_sync(FULL, id[j], o);
+                if (lane >= o && iv == id[j] && valid[j]) add_count(sum[j], flg[j], sv, fv);
+            }
+        }
+        {  // row 1's first run may continue row 0's last one (every lane
+           // takes part in the shuffles; only then do lanes branch)
+            const uint64_t s31 = __shfl_sync(FULL, sum[0], 31);
+            const uint32_t f31 = __shfl_sync(FULL, flg[0], 31);
+            const int i31 = __shfl_sync(FULL, id[0], 31);
+            const int v31 = __shfl_sync(FULL, (int)valid[0], 31);
+            if (valid[1] && v31 && id[1] == i31) add_count(sum[1], flg[1], s31, f31);
+        }
+        // the last element of each run holds its total
+        const uint32_t next0 = __shfl_down_sync(FULL, hub[0], 1);
+        const uint32_t first1 = __shfl_sync(FULL, hub[1], 0);
+        const uint32_t next1 = __shfl_down_sync(FULL, hub[1], 1);
+        bool cand[2];
+        cand[0] = valid[0] && (lane == 31 ? first1 != hub[0] : next0 != hub[0]);
+        cand[1] = valid[1] && (lane == 31 || next1 != hub[1]);
+        const int uniq = __popc(h0) + __popc(h1);
+        n_uniq += (unsigned long long)uniq;
+
+        // 4. rule 2: the landmark filter, then the undecided candidates' scans
+        bool surv[2] = {cand[0], cand[1]};
+        if (d >= 3 && uniq > 0) {
+            bool und[2] = {cand[0], cand[1]};
+            if (A.lmk) {
+                if (lane < A.lmk_stride / 4) ul[lane] = __ldg((const uint32_t*)(A.lmk + u * A.lmk_stride) + lane);
+                __syncwarp();
+                const uint32_t dd = (uint32_t)d * 0x00010001u;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (!cand[j]) continue;
+                    const uint4* row = (const uint4*)(A.lmk + (size_t)hub[j] * A.lmk_stride);
+                    uint32_t hit = 0, far = 0;
+                    for (int q4 = 0; q4 < A.lmk_words; ++q4) {
+                        const uint4 b4 = __ldg(row + q4);
+                        const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t a = ul[4 * q4 + q], b = bw[q];
+                            hit |= __vcmpltu2(__vaddus2(a, b), dd);
+                            const uint32_t known = ~(__vcmpeq2(a, 0xFFFFFFFFu) | __vcmpeq2(b, 0xFFFFFFFFu));
+                            far |= __vcmpgeu2(__vabsdiffu2(a, b), dd) & known;
+                        }
+                    }
+                    if (hit) {
+                        surv[j] = false;
+                        und[j] = false;
+                        ++n_lpr;
+                    } else if (far) {
+                        und[j] = false;
+                        ++n_lpv;
+                    }
+                }
+                __syncwarp();
+            }
+            unsigned u0 = __ballot_sync(FULL, und[0]), u1 = __ballot_sync(FULL, und[1]);
+            while (u0 | u1) {
+                const int j = u0 ? 0 : 1;
+                const unsigned m = j ? u1 : u0;
+                const int src = __ffs(m) - 1;
+                const uint32_t h = __shfl_sync(FULL, hub[j], src);
+                const bool pruned = scan_levels<32>(sm, A.seg, A.hub_arena, n, d, h, 1, d - 2, nullptr);
+                if (pruned && lane == src) surv[j] = false;
+                if (j) u1 &= m - 1; else u0 &= m - 1;
+            }
+        }
+
+        // 5. append the survivors in hub order
+        const unsigned s0 = __ballot_sync(FULL, surv[0]), s1 = __ballot_sync(FULL, surv[1]);
+        const int S = __popc(s0) + __popc(s1);
+        if (S > 0) {
+            unsigned long long b0 = 0;
+            if (lane == 0) {
+                b0 = atomicAdd(&A.stt->bump, (unsigned long long)S);
+                if (b0 + S > A.arena_cap) atomicOr(&A.stt->arena_overflow, 1);
+            }
+            b0 = __shfl_sync(FULL, b0, 0);
+            if (b0 + S <= A.arena_cap) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (!surv[j]) continue;
+                    const int pos = j ? __popc(s0) + __popc(s1 & lt) : __popc(s0 & lt);
+                    A.hub_arena[b0 + pos] = hub[j] | (flg[j] ? kOvfBit : 0u);
+                    A.cnt_arena[b0 + pos] = sum[j];
+                }
+                if (lane == 0) A.seg_out[u] = seg_pack(b0, (uint32_t)S);
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (n_uniq) atomicAdd(&A.stt->unique_total, n_uniq);
+        if (n_lpr) atomicAdd(&A.stt->lmk_pruned, n_lpr);
+        if (n_lpv) atomicAdd(&A.stt->lmk_proven, n_lpv);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Push paradigm.
 
 __global__ void k_arc_counts(int64_t arcs, const uint32_t* __restrict__ cnt_arc, int64_t* __restrict__ out) {
@@ -1201,6 +1452,15 @@ static void launch_level_nt(int map_kind, bool offchip, int grid, size_t smem_by
         k_level<kMapHash, false, NT><<<grid, NT, smem_bytes, st>>>(A);
     else
         k_level<kMapSeg, false, NT><<<grid, NT, smem_bytes, st>>>(A);
+}
+
+cudaError_t micro_kernel_occupancy(int* occupancy) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, (const void*)k_level_micro, kMicroThreads, 0);
+}
+
+cudaError_t launch_level_micro(int grid, const LevelArgs& A, cudaStream_t st) {
+    k_level_micro<<<grid, kMicroThreads, 0, st>>>(A);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_level(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,

@@ -15,8 +15,12 @@ constexpr int kLightThreads = 128;  // CTA of the level kernel for light vertice
 constexpr uint32_t kLightCap = 1024;  // candidate slots of a light vertex
 constexpr uint32_t kOffStartCap = 16384;    // first off-chip table size
 constexpr uint32_t kOffSlabCap = 1u << 17;  // off-chip slab of the first pass, in candidate slots
+constexpr int kMicroThreads = 256;    // the warp-per-vertex level kernel: 8 vertices per CTA
+constexpr int kMicroBucket = 6;       // micro: fewer than 2^6 pulled entries (64 fit a warp's registers)
 constexpr int kLightBucket = 9;       // light: fewer than 2^9 pulled entries, so at most 2 * 511 < kLightCap
                                       // slots are asked for, and the table never overflows
+constexpr int kWarpLevelsMax = 127;   // automatic warp-per-vertex levels: at most this deep,
+constexpr int kWarpLevelsFew = 32;    // and while the last level had under this many candidates per vertex
 constexpr int kArcChunk = kLevelThreads;  // arcs staged per gather chunk (the CTA size)
 
 // Resident CTAs per SM each kernel size is built for (64 registers a thread).
@@ -46,7 +50,7 @@ struct LevelStatus {
     int work_light;
     int n_giant;     // off-chip vertices whose candidates overflow the slab
     int work_giant;
-    int pad;
+    int work_micro;
     int bucket_cnt[kBuckets];
     int bucket_base[kBuckets];
     int bucket_fill[kBuckets];
@@ -178,5 +182,9 @@ cudaError_t launch_cost(int d, int64_t n, int64_t arcs, const int64_t* rp, const
 cudaError_t level_kernel_attrs(int map_kind, size_t smem_bytes, int* occupancy, int nt = kLevelThreads);
 cudaError_t launch_level(int map_kind, bool offchip, int grid, size_t smem_bytes, const LevelArgs& A,
                          cudaStream_t st, int nt = kLevelThreads);
+// The warp-per-vertex variant for vertices with fewer than 2^kMicroBucket
+// pulled entries (k_level_micro).
+cudaError_t micro_kernel_occupancy(int* occupancy);
+cudaError_t launch_level_micro(int grid, const LevelArgs& A, cudaStream_t st);
 
 }  // namespace pspc
