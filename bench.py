@@ -148,16 +148,16 @@ QUERY_SOURCES = ("pspc_query.cu", "pspc_internal.cuh")
 
 
 def profiled_traffic(name: str, workload: str, sources):
-    """DRAM bytes per launch from a committed ncu summary
-    (profiles/<name>_<workload>.json), if it was taken on the current
-    kernel sources; else None."""
+    """DRAM bytes per unit (a level of the level kernels, a query call) from
+    a committed ncu summary (profiles/<name>_<workload>.json), if it was
+    taken on the current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if kernel_source_sha(sources) != d.get("source_sha256"):
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("dram_bytes_per_unit")
 
 
 def reduce_max(vals, dist, device):
@@ -363,14 +363,19 @@ class Workload:
         achieved_q = qb / (qms / 1e3) / 1e9 if qms > 0 else 0.0
         traffic = profiled_traffic("k_level", workload, LEVEL_SOURCES)
         traffic_q = profiled_traffic("k_query", workload, QUERY_SOURCES)
-        roof = {"kernel": "k_level (pull gather + count merge + prune + append)", "bound": "hbm",
+        # achieved: algorithmic bytes / device time; traffic: DRAM bytes of
+        # one unit from the committed ncu summary (null when the kernel
+        # sources changed since), and the DRAM rate it implies
+        roof = {"kernel": "level kernels: pull gather + count merge + prune + append", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
-                "peak_kind": peak_kind, "traffic": traffic,
+                "peak_kind": peak_kind, "traffic": traffic, "traffic_unit": "one level",
                 "dram_gbs": (traffic * kl / (kms / 1e3) / 1e9) if (traffic and kms) else None,
-                "bytes_per_step": kb / K, "kernel_ms_per_step": kms / K, "launches_per_step": kl / K}
+                "bytes_per_step": kb / K, "kernel_ms_per_step": kms / K, "levels_per_step": kl / K}
         roof_q = {"kernel": "query call: source grouping + merge-join (Eq. (1)-(2))", "bound": "hbm",
                   "achieved": achieved_q, "peak": peak, "unit": "GB/s", "frac": achieved_q / peak if peak else None,
-                  "peak_kind": peak_kind, "traffic": traffic_q, "bytes_per_step": qb / K, "ms_per_step": qms / K}
+                  "peak_kind": peak_kind, "traffic": traffic_q, "traffic_unit": "one query call of one graph",
+                  "dram_gbs": (traffic_q * len(self.W) * K / (qms / 1e3) / 1e9) if (traffic_q and qms) else None,
+                  "bytes_per_step": qb / K, "ms_per_step": qms / K, "calls_per_step": len(self.W)}
         return per_graph, roof, roof_q
 
 

@@ -41,8 +41,10 @@ extern "C" {
 #define PSPC_E_INVAL 1   /* malformed graph, rank, pair or argument */
 #define PSPC_E_NOMEM 2   /* device or host allocation failed */
 #define PSPC_E_CUDA 3    /* a CUDA runtime call or kernel failed */
-#define PSPC_E_TIMEOUT 4 /* a bounded device-side wait gave up */
-#define PSPC_E_DIST 5    /* a shortest distance exceeds 32767 */
+/* 4 is not used: no kernel of the library waits on another kernel, a flag
+ * or a peer, so there is no device-side wait that could time out. */
+#define PSPC_E_DIST 5    /* a label distance exceeds the limit (32767 or
+                            pspc_opts.max_levels) */
 
 /* Unreachable marker in query and export distances. */
 #define PSPC_UNREACHED 0xFFFFu
@@ -52,7 +54,10 @@ extern "C" {
  * col:     int32[row_ptr[n]]; the neighbours of v are col[row_ptr[v] ..
  *          row_ptr[v+1]), strictly ascending (so no duplicate arcs), no
  *          self-loop, and every arc u->v has its reverse v->u.
- * 1 <= n < 2^24. Violations make pspc_build return PSPC_E_INVAL. */
+ * 1 <= n < 2^24. Violations make pspc_build return PSPC_E_INVAL. The
+ * strictly ascending rows are how the library rejects duplicate arcs (an
+ * undirected simple graph, Section "Preliminaries"); the library then
+ * relabels the vertices by rank and sorts each row again in rank space. */
 typedef struct {
     int64_t n;
     const int64_t* row_ptr;
@@ -254,7 +259,9 @@ int pspc_query_async(const pspc_index* ix, const int32_t* pairs, int64_t q, uint
 
 /*
  * pspc_export -- copy the index to host arrays, by caller vertex id, each
- * label listed by hub rank (highest first), hubs given as caller ids.
+ * label listed by hub rank (highest first), hubs given as caller ids: the
+ * layout of the paper's Table "Shortest Path Counting Labels", where each
+ * vertex's entries (hub, distance, count) follow the vertex order.
  * off: int64[n+1]; hub: int32[E]; dist: uint16[E]; cnt: uint64[E];
  * ovf: uint8[E] (E = pspc_stats().entries). All host memory owned by the
  * caller. Errors: PSPC_E_INVAL, PSPC_E_NOMEM, PSPC_E_CUDA.
@@ -282,7 +289,10 @@ int pspc_export_vertices(const pspc_index* ix, const int32_t* verts, int64_t k, 
  */
 int pspc_hub_column(const pspc_index* ix, int32_t w, uint16_t* dist, uint64_t* cnt, uint8_t* ovf);
 
-/* pspc_stats -- sizes and timings of an index (host struct). */
+/* pspc_stats -- sizes and timings of an index (host struct): vertices,
+ * arcs, label entries (the index size the paper reports in Section
+ * "Experiments"), levels (the largest label distance + 1, Theorem "Distance
+ * Dependency"), device bytes, kernel launches and device times. */
 int pspc_stats(const pspc_index* ix, pspc_stats_t* s);
 
 /* pspc_level_stats -- copy up to `cap` per-level records (level 1 first) to
@@ -351,15 +361,16 @@ int pspc_landmarks(const pspc_index* ix, int32_t* k, uint16_t* dist);
 
 /*
  * pspc_inject_alloc_failure -- fault injection for tests of the library's
- * out-of-memory paths (the paper has no counterpart). After this call the
+ * error paths (the paper has no counterpart). After this call the
  * library's next `after` device allocations succeed and every later one
- * fails as if the device were out of memory: the call that needed it
- * returns PSPC_E_NOMEM, releases what it holds, and leaves *out = NULL for
- * a build. after < 0 removes the limit (the default). Process-wide, for
- * every device; pspc_query_noalloc allocates nothing and is unaffected.
- * Returns PSPC_OK.
+ * fails, reporting `status`: PSPC_E_NOMEM as if the device were out of
+ * memory, or PSPC_E_CUDA as another CUDA error. The call that needed the
+ * allocation returns that status, releases what it holds, and leaves
+ * *out = NULL for a build. after < 0 removes the limit (the default).
+ * Process-wide, for every device; pspc_query_noalloc allocates nothing and
+ * is unaffected. Errors: PSPC_E_INVAL (another status).
  */
-int pspc_inject_alloc_failure(int64_t after);
+int pspc_inject_alloc_failure(int64_t after, int32_t status);
 
 /* pspc_free -- release an index and all its device memory; NULL is a no-op. */
 void pspc_free(pspc_index* ix);

@@ -26,7 +26,6 @@ PSPC_QUERY_BY_SOURCE = 1
 PSPC_E_INVAL = 1
 PSPC_E_NOMEM = 2
 PSPC_E_CUDA = 3
-PSPC_E_TIMEOUT = 4
 PSPC_E_DIST = 5
 UNREACHED = 0xFFFF
 
@@ -91,7 +90,7 @@ _SIGS = {
     "pspc_hub_column": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "pspc_query_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "pspc_landmarks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), _P]),
-    "pspc_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
+    "pspc_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32]),
     "pspc_free": (None, [_P]),
     "pspc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -116,11 +115,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
         return lib
 
 
-def inject_alloc_failure(after: int) -> None:
+def inject_alloc_failure(after: int, status: int = PSPC_E_NOMEM) -> None:
     """pspc_inject_alloc_failure: the library's next ``after`` device
-    allocations succeed and later ones fail (PSPC_E_NOMEM); ``after`` < 0
-    removes the limit. For tests of the out-of-memory paths."""
-    load().pspc_inject_alloc_failure(int(after))
+    allocations succeed and later ones fail with ``status`` (PSPC_E_NOMEM
+    or PSPC_E_CUDA); ``after`` < 0 removes the limit. For tests of the
+    error paths."""
+    rc = load().pspc_inject_alloc_failure(int(after), int(status))
+    if rc != PSPC_OK:
+        raise PSPCError(rc, "pspc_inject_alloc_failure")
 
 
 def strerror(code: int) -> str:

@@ -33,6 +33,7 @@ static bool g_pool_ok[64];
 // Allocation-failure injection (pspc_inject_alloc_failure): the number of
 // library device allocations still allowed to succeed, or -1 (no limit).
 static std::atomic<int64_t> g_alloc_budget{-1};
+static std::atomic<int> g_alloc_error{(int)cudaErrorMemoryAllocation};  // what an injected failure returns
 
 static bool alloc_allowed() {
     int64_t b = g_alloc_budget.load(std::memory_order_relaxed);
@@ -46,7 +47,7 @@ static bool alloc_allowed() {
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
     if (!alloc_allowed()) {
         *p = nullptr;
-        return cudaErrorMemoryAllocation;
+        return (cudaError_t)g_alloc_error.load(std::memory_order_relaxed);
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -175,7 +176,10 @@ int exclusive_scan_i64(int64_t* a, int64_t n, cudaStream_t st, int64_t* launches
 
 using namespace pspc;
 
-extern "C" int pspc_inject_alloc_failure(int64_t after) {
+extern "C" int pspc_inject_alloc_failure(int64_t after, int32_t status) {
+    if (status != PSPC_E_NOMEM && status != PSPC_E_CUDA) return PSPC_E_INVAL;
+    g_alloc_error.store(status == PSPC_E_NOMEM ? (int)cudaErrorMemoryAllocation : (int)cudaErrorInvalidValue,
+                        std::memory_order_relaxed);
     g_alloc_budget.store(after < 0 ? -1 : after, std::memory_order_relaxed);
     return PSPC_OK;
 }
@@ -186,7 +190,6 @@ extern "C" const char* pspc_strerror(int code) {
         case PSPC_E_INVAL: return "invalid argument (graph, rank, pair or option)";
         case PSPC_E_NOMEM: return "out of memory";
         case PSPC_E_CUDA: return "CUDA error";
-        case PSPC_E_TIMEOUT: return "bounded device wait timed out";
         case PSPC_E_DIST: return "distance limit exceeded";
         default: return "unknown status";
     }

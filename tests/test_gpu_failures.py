@@ -1,8 +1,11 @@
 """Host-side failure paths of the C ABI, on the GPU but without a GPU fault:
 the distance limit (PSPC_E_DIST) at a caller's max_levels and at the 15-bit
-storage limit of 32767, and out-of-memory (PSPC_E_NOMEM) injected on the
-host at every device allocation of a build and of a query. After each
-failure the library keeps working and its results still equal the oracle."""
+storage limit of 32767, and allocation failures injected on the host
+(PSPC_E_NOMEM, or PSPC_E_CUDA for another CUDA error) at every device
+allocation of a build and of a query. After each failure the library keeps
+working and its results still equal the oracle. With PSPC_E_INVAL (tested
+with the bad inputs of the parity tests) every status the header declares
+is reached."""
 from __future__ import annotations
 
 import numpy as np
@@ -95,20 +98,22 @@ def test_distance_storage_limit_32767(pspc):
         oracle.OracleIndex(g2, rank2)
 
 
-@pytest.mark.parametrize("name,kw", [("ba2000", {}), ("grid32", {"map_kind": 2}),
-                                     ("rmat12_ef16", {"paradigm": 1})])
-def test_out_of_memory_at_every_allocation_of_a_build(pspc, name, kw):
-    """Allocation k of a build fails, for every k: the build reports
-    PSPC_E_NOMEM and returns no index; with no failure it succeeds, and the
+@pytest.mark.parametrize("name,kw,status", [("ba2000", {}, "NOMEM"), ("grid32", {"map_kind": 2}, "NOMEM"),
+                                            ("rmat12_ef16", {"paradigm": 1}, "NOMEM"), ("grid32", {}, "CUDA")])
+def test_failure_at_every_allocation_of_a_build(pspc, name, kw, status):
+    """Allocation k of a build fails, for every k, as out of memory or as
+    another CUDA error: the build reports that status (PSPC_E_NOMEM or
+    PSPC_E_CUDA) and returns no index; with no failure it succeeds, and the
     index equals the oracle's."""
     g, rank, _ = P.workload(name)
+    code = pspc.PSPC_E_NOMEM if status == "NOMEM" else pspc.PSPC_E_CUDA
     k = 0
     while True:
-        pspc.inject_alloc_failure(k)
+        pspc.inject_alloc_failure(k, code)
         try:
             ix = pspc.Index.from_graph(g, rank, **kw)
         except pspc.PSPCError as e:
-            assert e.code == pspc.PSPC_E_NOMEM, (k, e)
+            assert e.code == code, (k, e)
             k += 1
             assert k < 2000
             continue
