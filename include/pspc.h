@@ -305,14 +305,19 @@ int pspc_level_stats(const pspc_index* ix, pspc_level_stat_t* out, int32_t cap,
  * merge-joined. 8, 16 or 32 = that many lanes compare 32-bit hub words held
  * in registers; 64, 128 or 256 = one warp stages chunks of that many
  * entries of both labels in shared memory; PSPC_QUERY_BY_SOURCE = pairs
- * sorted by source, L(s) held in an on-chip hash for every pair of that
- * source and each pair streams only L(t) (used when the call groups its
- * pairs by source, q >= 4096 and q >= n/4, and the largest label has at
- * most 12,287 entries; otherwise 0 applies); 0 = PSPC_QUERY_BY_SOURCE when
- * it applies and q >= 64 n, else chosen from the average label size.
- * Results do not depend on it. Errors: PSPC_E_INVAL.
+ * sorted by source, L(s) held on chip for every pair of that source and
+ * each pair streams only L(t): as a table of every vertex's position in
+ * L(s) when 2 bytes per vertex plus 2 per entry of the largest label fit
+ * in 224 KB, else as a hash of L(s); PSPC_QUERY_BY_SOURCE_HASH = the hash
+ * form even where the table fits. Both apply when the call groups its
+ * pairs by source (q >= 4096 and q >= n/4); the hash needs a largest label
+ * of at most 12,287 entries. Where the chosen form does not apply, 0
+ * applies. 0 = PSPC_QUERY_BY_SOURCE when it applies and q >= 64 n, else
+ * chosen from the average label size. Results do not depend on it.
+ * Errors: PSPC_E_INVAL.
  */
 #define PSPC_QUERY_BY_SOURCE 1
+#define PSPC_QUERY_BY_SOURCE_HASH 2
 int pspc_set_query_group(pspc_index* ix, int32_t lanes);
 
 /*

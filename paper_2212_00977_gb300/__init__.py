@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_cuda_build", "libpspc.so")
 
 PSPC_OK = 0
 PSPC_QUERY_BY_SOURCE = 1
+PSPC_QUERY_BY_SOURCE_HASH = 2
 PSPC_E_INVAL = 1
 PSPC_E_NOMEM = 2
 PSPC_E_CUDA = 3
@@ -264,8 +265,9 @@ class Index:
 
     def set_query_group(self, lanes: int) -> None:
         """Query variant of pspc_query: 8/16/32 lanes per pair, 64/128/256
-        staged chunk entries, PSPC_QUERY_BY_SOURCE (on-chip hash of L(s) for
-        the pairs of each source), or 0 = automatic."""
+        staged chunk entries, PSPC_QUERY_BY_SOURCE (L(s) on chip for the
+        pairs of each source: a position table when it fits, else a hash),
+        PSPC_QUERY_BY_SOURCE_HASH (the hash form), or 0 = automatic."""
         rc = load().pspc_set_query_group(self._h, int(lanes))
         if rc != PSPC_OK:
             raise PSPCError(rc, "pspc_set_query_group")

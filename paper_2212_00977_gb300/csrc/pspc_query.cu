@@ -42,6 +42,7 @@ struct QueryArgs {
     const uint64_t* cnt;
     const int32_t* pairs;
     const int32_t* perm;  // processing order of the pairs (grouped by source), or NULL
+    const unsigned long long* src_end;  // with perm: end of each source's pairs in it (bucket n: invalid ids)
     int64_t q;
     uint16_t* out_dist;
     uint64_t* out_cnt;
@@ -423,6 +424,204 @@ __global__ void __launch_bounds__(kBySourceThreads) k_query_by_source(const Quer
     }
 }
 
+// One step of L(t) for a lane: entries j0 + 32 u + lane (hub kNoHub past
+// the end of the label).
+__device__ __forceinline__ void load_step(const int32_t* __restrict__ hubt, const uint16_t* __restrict__ distt,
+                                          uint32_t j0, uint32_t lb, int lane, uint32_t (&hb)[kBySourceUnroll],
+                                          uint32_t (&db)[kBySourceUnroll]) {
+    if (j0 + 32 * kBySourceUnroll <= lb) {
+#pragma unroll
+        for (int u = 0; u < kBySourceUnroll; ++u) {
+            hb[u] = (uint32_t)__ldg(hubt + j0 + 32 * u + lane);
+            db[u] = __ldg(distt + j0 + 32 * u + lane);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < kBySourceUnroll; ++u) {
+            const uint32_t j = j0 + 32 * u + lane;
+            hb[u] = j < lb ? (uint32_t)__ldg(hubt + j) : kNoHub;
+            db[u] = j < lb ? __ldg(distt + j) : 0u;
+        }
+    }
+}
+
+// Source bucket of sorted pair r (n for a source outside [0, n)).
+__device__ __forceinline__ int64_t run_bucket(const QueryArgs& Q, int64_t r) {
+    const int32_t v = __ldg(Q.pairs + 2 * (int64_t)__ldg(Q.perm + r));
+    return (v >= 0 && v < Q.n) ? (int64_t)v : Q.n;
+}
+
+// Entries of the by-source candidate list of a warp: matches at the pair's
+// running minimum (position in L(t) << 16 | position in L(s) << 1 | a
+// factor's flag), whose counts are read together once the list is full or
+// the pair is done.
+constexpr uint32_t kBySourceCand = 256;
+
+// Adds the count products of the warp's list to the lanes' partial sums:
+// lane i takes entries i, i + 32, ..., so the loads are independent.
+__device__ __forceinline__ void add_candidates(const QueryArgs& Q, int64_t a0, const unsigned long long* cntt,
+                                               const uint32_t* cw, uint32_t nc, int lane, uint64_t& sum,
+                                               uint32_t& flag) {
+    __syncwarp();
+    for (uint32_t c = lane; c < nc; c += 32) {
+        const uint32_t v = cw[c];
+        const uint64_t ca = __ldg((const unsigned long long*)Q.cnt + a0 + ((v >> 1) & 0x7FFFu));
+        const uint64_t cb = __ldg(cntt + (v >> 16));
+        add_term(sum, flag, ca * cb, (v & 1u) | (uint32_t)(__umul64hi(ca, cb) != 0));
+    }
+    __syncwarp();
+}
+
+// The by-source query with direct addressing, for graphs whose vertex
+// count fits on chip: pos[h] is the position of hub h in L(s) (0xFFFF:
+// absent) and sd[i] the distance of L(s) entry i. Hubs are ranks in
+// [0, n), so a lookup is one 2-byte shared-memory read with no probe chain
+// (the hash above has chains of several 8-byte reads whose length varies
+// across the lanes of a warp). pos is cleared once per CTA; a run sets the
+// positions of its L(s) and resets them to 0xFFFF when its pairs are done.
+// An item of kBySourceItem sorted pairs owns the runs that start in it and
+// takes each whole (its end comes from the grouping sort's bucket ends),
+// so every source's L(s) is set up once. The run's pairs are handed to
+// warps from a shared counter. Per pair, L(t) streams in steps of
+// 32 x kBySourceUnroll entries with the next step's loads in flight; a
+// step finds, from shared memory alone, the smallest distance sum among its
+// matches over the whole warp, and the matches at the pair's running
+// minimum join a per-warp list in shared memory. Counts are read only for
+// the list, once per pair (or when it fills), all loads independent: reads
+// at every match that reached a lane's minimum so far cost one 32-byte
+// sector each and one load round trip each inside the stream.
+__global__ void __launch_bounds__(kBySourceThreads)
+    k_query_by_source_direct(const QueryArgs Q, uint32_t n_pad, uint32_t label_pad) {
+    extern __shared__ uint16_t dsm[];
+    uint16_t* pos = dsm;         // n_pad entries (even)
+    uint16_t* sd = dsm + n_pad;  // entries of the largest label (label_pad: even)
+    __shared__ unsigned long long s_next;
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint32_t* cw = (uint32_t*)(dsm + n_pad + label_pad) + (tid >> 5) * kBySourceCand;  // the warp's list
+    for (uint32_t i = tid; i < n_pad; i += blockDim.x) pos[i] = 0xFFFFu;
+    __syncthreads();
+    const int64_t items = (Q.q + kBySourceItem - 1) / kBySourceItem;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        // the runs that start in [kb, ke), each in full (one L(s) setup per source)
+        const int64_t kb = item * kBySourceItem;
+        const int64_t ke = Q.q - kb < kBySourceItem ? Q.q : kb + kBySourceItem;
+        int64_t r0 = kb;
+        {
+            const int64_t b = run_bucket(Q, r0);
+            const int64_t start = b > 0 ? (int64_t)__ldg(Q.src_end + b - 1) : 0;
+            if (start < kb) r0 = (int64_t)__ldg(Q.src_end + b);  // that run belongs to an earlier item
+        }
+        while (r0 < ke) {
+            const int64_t b = run_bucket(Q, r0);
+            const int64_t r1 = (int64_t)__ldg(Q.src_end + b);
+            const int32_t s = (int32_t)b;
+            if (b >= Q.n) {  // the sort puts every invalid source in bucket n
+                for (int64_t r = r0 + tid; r < r1; r += blockDim.x) {
+                    const int64_t p = __ldg(Q.perm + r);
+                    atomicOr(Q.err, 1);
+                    write_fixed(Q, p, PSPC_UNREACHED, 0);
+                }
+                r0 = r1;
+                continue;
+            }
+            const int32_t rs = __ldg(Q.rank + s);
+            const int64_t a0 = __ldg(Q.off + rs);
+            const uint32_t la = (uint32_t)(__ldg(Q.off + rs + 1) - a0);
+            for (uint32_t i = tid; i < la; i += blockDim.x) {
+                pos[__ldg(Q.hub + a0 + i)] = (uint16_t)i;
+                sd[i] = __ldg(Q.dist + a0 + i);
+            }
+            if (tid == 0) s_next = (unsigned long long)r0;
+            __syncthreads();
+            for (;;) {
+                unsigned long long r = 0;
+                if (lane == 0) r = atomicAdd(&s_next, 1ull);
+                r = __shfl_sync(0xFFFFFFFFu, r, 0);
+                if ((int64_t)r >= r1) break;
+                const int64_t p = __ldg(Q.perm + r);
+                const int32_t t = __ldg(Q.pairs + 2 * p + 1);
+                if (t < 0 || t >= Q.n) {
+                    if (lane == 0) {
+                        atomicOr(Q.err, 1);
+                        write_fixed(Q, p, PSPC_UNREACHED, 0);
+                    }
+                    continue;
+                }
+                if (t == s) {
+                    if (lane == 0) write_fixed(Q, p, 0, 1);
+                    continue;
+                }
+                const int32_t rt = __ldg(Q.rank + t);
+                const int64_t b0 = __ldg(Q.off + rt);
+                const int64_t lb = __ldg(Q.off + rt + 1) - b0;
+                const int32_t* hubt = Q.hub + b0;
+                const uint16_t* distt = Q.dist + b0;
+                const unsigned long long* cntt = (const unsigned long long*)Q.cnt + b0;
+                uint32_t best = 0xFFFFu;  // the pair's minimum distance sum so far (0xFFFF: none)
+                uint64_t sum = 0;
+                uint32_t flag = 0;
+                uint32_t nc = 0;  // entries in the warp's list (warp-uniform)
+                // L(t) in steps of 32 x kBySourceUnroll entries; the next step's
+                // loads are in flight while this step probes
+                const uint32_t lbu = (uint32_t)lb;
+                uint32_t nh[kBySourceUnroll], nd[kBySourceUnroll];
+                load_step(hubt, distt, 0, lbu, lane, nh, nd);
+                for (uint32_t j0 = 0; j0 < lbu; j0 += 32 * kBySourceUnroll) {
+                    uint32_t hb[kBySourceUnroll], db[kBySourceUnroll];
+#pragma unroll
+                    for (int u = 0; u < kBySourceUnroll; ++u) {
+                        hb[u] = nh[u];
+                        db[u] = nd[u];
+                    }
+                    if (j0 + 32 * kBySourceUnroll < lbu) load_step(hubt, distt, j0 + 32 * kBySourceUnroll, lbu, lane, nh, nd);
+                    // key of a match: distance sum << 16 | L(s) position (15 bits) << 1 | a factor's flag
+                    uint32_t key[kBySourceUnroll];
+                    uint32_t kmin = 0xFFFFFFFFu;
+#pragma unroll
+                    for (int u = 0; u < kBySourceUnroll; ++u) {
+                        const uint32_t ia = hb[u] == kNoHub ? 0xFFFFu : (uint32_t)pos[hb[u]];
+                        const uint32_t da = ia == 0xFFFFu ? 0u : (uint32_t)sd[ia];
+                        key[u] = ia == 0xFFFFu ? 0xFFFFFFFFu
+                                               : ((da & 0x7FFFu) + (db[u] & 0x7FFFu)) << 16 | ia << 1 | ((da | db[u]) >> 15);
+                        kmin = min(kmin, key[u]);
+                    }
+                    // the matches at the running minimum join the warp's list
+                    uint32_t cmin = kmin >> 16;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cmin = min(cmin, __shfl_xor_sync(0xFFFFFFFFu, cmin, o));
+                    if (cmin == 0xFFFFu || cmin > best) continue;  // warp-uniform
+                    if (cmin < best) {  // a smaller sum: what the list and the sum hold is superseded
+                        best = cmin;
+                        nc = 0;
+                        sum = 0;
+                        flag = 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kBySourceUnroll; ++u) {
+                        const bool hit = (key[u] >> 16) == best;
+                        const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+                        if (m == 0) continue;
+                        if (nc + (uint32_t)__popc(m) > kBySourceCand) {  // rare: a full list
+                            add_candidates(Q, a0, cntt, cw, nc, lane, sum, flag);
+                            nc = 0;
+                        }
+                        if (hit)
+                            cw[nc + (uint32_t)__popc(m & ((1u << lane) - 1u))] =
+                                (j0 + 32 * u + lane) << 16 | (key[u] & 0xFFFFu);
+                        nc += (uint32_t)__popc(m);
+                    }
+                }
+                add_candidates(Q, a0, cntt, cw, nc, lane, sum, flag);
+                finish_pair_warp(Q, p, best == 0xFFFFu ? 0xFFFFFFFFu : best, sum, flag, lane);
+            }
+            __syncthreads();
+            for (uint32_t i = tid; i < la; i += blockDim.x) pos[__ldg(Q.hub + a0 + i)] = 0xFFFFu;
+            __syncthreads();
+            r0 = r1;
+        }
+    }
+}
+
 // Grouping by source: a counting sort of the pair indices by s, so that the
 // pairs sharing a source run back to back and reuse L(s) from cache. Ids
 // outside [0, n) go to an extra bucket n (they are rejected later).
@@ -453,12 +652,19 @@ static void prefer_max_shared(const void* fn) {
 static std::once_flag g_carveout_once;
 
 constexpr uint32_t kBySourceMaxSlots = 16384;  // 128 KB of table
+// Shared memory the direct-address variant may take: 2 bytes per vertex and
+// per entry of the largest label (within the 227 KB a CTA can have, less
+// the kernel's static arrays).
+constexpr size_t kBySourceDirectBytes = 224 * 1024;
 
 static void set_query_carveouts() {
     std::call_once(g_carveout_once, [] {
         prefer_max_shared((const void*)k_query_by_source);
         cudaFuncSetAttribute((const void*)k_query_by_source, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kBySourceMaxSlots * 8));
+        prefer_max_shared((const void*)k_query_by_source_direct);
+        cudaFuncSetAttribute((const void*)k_query_by_source_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kBySourceDirectBytes);
         prefer_max_shared((const void*)k_query<8>);
         prefer_max_shared((const void*)k_query<16>);
         prefer_max_shared((const void*)k_query<32>);
@@ -475,6 +681,23 @@ static uint32_t by_source_slots(const Index& ix) {
     return s <= kBySourceMaxSlots ? s : 0u;
 }
 
+// Positions of the largest label the direct-address by-source kernel keeps
+// in shared memory (rounded up to even, so the lists after them are 4-byte
+// aligned).
+static uint32_t by_source_label_pad(const Index& ix) {
+    return (uint32_t)(((ix.max_label > 0 ? ix.max_label : 1) + 1) & ~(int64_t)1);
+}
+
+// Shared-memory bytes of the direct-address by-source kernel's vertex
+// positions and largest label (0: with the candidate lists of a 1024-thread
+// CTA they do not fit on chip, or a position does not fit the 15 bits the
+// kernel keeps of it).
+static size_t by_source_direct_bytes(const Index& ix) {
+    if (ix.max_label > 0x7FFF) return 0;
+    const size_t b = 2 * (size_t)((ix.n + 1) & ~(int64_t)1) + 2 * (size_t)by_source_label_pad(ix);
+    return b + (size_t)(kBySourceThreads / 32) * kBySourceCand * 4 <= kBySourceDirectBytes ? b : 0;
+}
+
 // The query kernel. Automatic choice: by source when the pairs are grouped,
 // L(s) fits on chip and sources repeat often (q >= 64 n: each table build
 // serves many pairs; with fewer pairs per source the staged merge-join,
@@ -483,9 +706,12 @@ static uint32_t by_source_slots(const Index& ix) {
 // labels (fewer merge steps), narrow groups for short ones (more pairs in
 // flight per warp), warp-staged chunks of 256 entries for long labels.
 static int query_group_for(const Index& ix, bool grouped, int64_t q) {
-    const bool by_source_ok = grouped && by_source_slots(ix) > 0;
+    const bool by_source_ok = grouped && (by_source_direct_bytes(ix) > 0 || by_source_slots(ix) > 0);
     if (ix.query_group == PSPC_QUERY_BY_SOURCE && by_source_ok) return PSPC_QUERY_BY_SOURCE;
-    if (ix.query_group && ix.query_group != PSPC_QUERY_BY_SOURCE) return ix.query_group;
+    if (ix.query_group == PSPC_QUERY_BY_SOURCE_HASH && grouped && by_source_slots(ix) > 0)
+        return PSPC_QUERY_BY_SOURCE_HASH;
+    if (ix.query_group && ix.query_group != PSPC_QUERY_BY_SOURCE && ix.query_group != PSPC_QUERY_BY_SOURCE_HASH)
+        return ix.query_group;
     if (ix.query_group == 0 && by_source_ok && q >= 64 * ix.n) return PSPC_QUERY_BY_SOURCE;
     const double avg = ix.n ? (double)ix.entries / (double)ix.n : 0.0;
     return avg >= 128.0 ? 256 : (avg >= 24.0 ? 16 : 8);
@@ -506,7 +732,21 @@ static cudaError_t launch_query(Index& ix, const QueryArgs& Q, cudaStream_t st) 
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
     if (e != cudaSuccess) return e;
     __atomic_fetch_add(&ix.query_launches, (int64_t)1, __ATOMIC_RELAXED);
-    if (G == PSPC_QUERY_BY_SOURCE) {
+    if (G == PSPC_QUERY_BY_SOURCE && by_source_direct_bytes(ix) > 0) {
+        // positions above a ninth of the shared memory leave room for one CTA
+        // per SM: make it a large one; smaller tables share SMs
+        const size_t base = by_source_direct_bytes(ix);
+        const int threads = base > (size_t)24 * 1024 ? kBySourceThreads : kQueryThreads;
+        const size_t smem = base + (size_t)(threads / 32) * kBySourceCand * 4;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_query_by_source_direct, threads, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t items = (Q.q + kBySourceItem - 1) / kBySourceItem;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * std::max(occ, 1)));
+        k_query_by_source_direct<<<grid, threads, smem, st>>>(Q, (uint32_t)((ix.n + 1) & ~(int64_t)1),
+                                                             by_source_label_pad(ix));
+        return cudaGetLastError();
+    }
+    if (G == PSPC_QUERY_BY_SOURCE || G == PSPC_QUERY_BY_SOURCE_HASH) {
         const uint32_t slots = by_source_slots(ix);
         const size_t smem = (size_t)slots * 8;
         // tables above a quarter of the shared memory leave room for one CTA
@@ -678,6 +918,7 @@ extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q,
     if (e == cudaSuccess && rc == PSPC_OK) {
         QueryArgs Q;
         Q.perm = d_perm;
+        Q.src_end = (const unsigned long long*)d_bins;
         Q.n = ix.n;
         Q.rank = ix.rank;
         Q.off = ix.off;
@@ -714,8 +955,8 @@ extern "C" int pspc_query(const pspc_index* hc, const int32_t* pairs, int64_t q,
 }
 
 extern "C" int pspc_set_query_group(pspc_index* h, int32_t lanes) {
-    if (!h || !(lanes == 0 || lanes == PSPC_QUERY_BY_SOURCE || lanes == 8 || lanes == 16 || lanes == 32 ||
-                lanes == 64 || lanes == 128 || lanes == 256))
+    if (!h || !(lanes == 0 || lanes == PSPC_QUERY_BY_SOURCE || lanes == PSPC_QUERY_BY_SOURCE_HASH || lanes == 8 ||
+                lanes == 16 || lanes == 32 || lanes == 64 || lanes == 128 || lanes == 256))
         return PSPC_E_INVAL;
     h->ix.query_group = lanes;
     if (h->ix.core) h->ix.core->ix.query_group = lanes;  // the core index runs the queries
@@ -819,6 +1060,7 @@ extern "C" int pspc_query_noalloc(const pspc_index* hc, const int32_t* pairs, in
             Q.cnt = ix.cnt;
             Q.pairs = pairs;
             Q.perm = d_perm;
+            Q.src_end = (const unsigned long long*)d_bins;
             Q.q = q;
             Q.out_dist = dist;
             Q.out_cnt = count;
@@ -864,6 +1106,7 @@ extern "C" int pspc_query_async(const pspc_index* hc, const int32_t* pairs, int6
     Q.cnt = ix.cnt;
     Q.pairs = pairs;
     Q.perm = nullptr;
+    Q.src_end = nullptr;
     Q.q = q;
     Q.out_dist = dist;
     Q.out_cnt = count;

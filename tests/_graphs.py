@@ -39,6 +39,13 @@ def grid(k: int) -> Graph:
     return csr_from_edges(k * k, np.array(e), f"grid{k}")
 
 
+def bipartite_2m(m: int) -> Graph:
+    """K(2, m): middle vertices 0..m-1, each joined to s = m and t = m + 1.
+    SPC(s, t) = (2, m); two middle vertices are at distance 2 with 2 paths."""
+    e = [(w, m) for w in range(m)] + [(w, m + 1) for w in range(m)]
+    return csr_from_edges(m + 2, np.array(e), f"K2,{m}")
+
+
 def hypercube(k: int) -> Graph:
     n = 1 << k
     e = [(v, v ^ (1 << b)) for v in range(n) for b in range(k) if v < v ^ (1 << b)]

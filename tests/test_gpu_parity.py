@@ -264,12 +264,58 @@ def test_query_group_invariance(pspc):
         ix = gpu_index(pspc, g, rank)
         pairs = pairs_fn(100000)
         rd, rc, rf, _ = ref.query(pairs)
-        for lanes in (8, 16, 32, 64, 128, 256, pspc.PSPC_QUERY_BY_SOURCE, 0):
+        for lanes in (8, 16, 32, 64, 128, 256, pspc.PSPC_QUERY_BY_SOURCE, pspc.PSPC_QUERY_BY_SOURCE_HASH, 0):
             ix.set_query_group(lanes)
             d, c, f = gpu_query(ix, pairs)
             assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
         with pytest.raises(pspc.PSPCError):
             ix.set_query_group(12)
+
+
+def test_query_variants_long_labels(pspc):
+    """Labels many chunks long (grid 128: hundreds to thousands of entries,
+    many hubs tied at the minimum): every query variant, including the
+    by-source position table and hash, equals breadth-first path counting. Runs of 100 pairs per source and uniform pairs."""
+    g, rank, pairs_fn = P.workload("grid128")
+    rng = np.random.default_rng(5)
+    src = rng.integers(0, g.n, 300)
+    runs = np.stack([np.repeat(src, 100), rng.integers(0, g.n, 30000)], axis=1)
+    pairs = np.concatenate([runs, pairs_fn(20000)]).astype(np.int32)
+    pairs = pairs[rng.permutation(len(pairs))]
+    rd, rc, rf, _ = oracle.spc_pairs(g, pairs)
+    ix = gpu_index(pspc, g, rank)
+    sizes = ix.label_sizes()
+    assert sizes.max() > 1000 and sizes.mean() > 256
+    for lanes in (pspc.PSPC_QUERY_BY_SOURCE, pspc.PSPC_QUERY_BY_SOURCE_HASH, 256, 128, 64, 32, 8, 0):
+        ix.set_query_group(lanes)
+        d, c, f = gpu_query(ix, pairs)
+        assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
+    ix.free()
+
+
+def test_by_source_many_tied_hubs(pspc):
+    """K(2, m) with the middle ranked first: L(s) and L(t) share m hubs, all
+    at distance sum 2, so one pair has m matches tied at the minimum (more
+    than a warp's on-chip list of them holds); every variant returns (2, m)
+    for (s, t) and (2, 2) between middle vertices, as the oracle does."""
+    m = 700
+    g = G.bipartite_2m(m)
+    rank = np.arange(g.n, dtype=np.int32)
+    rng = np.random.default_rng(2)
+    st = np.tile(np.array([[m, m + 1], [m + 1, m]], np.int32), (3000, 1))
+    mid = rng.integers(0, m, (4000, 2)).astype(np.int32)
+    pairs = np.concatenate([st, mid])
+    pairs = pairs[rng.permutation(len(pairs))]
+    rd, rc, rf, _ = oracle.OracleIndex(g, rank).query(pairs)
+    assert rd[(pairs[:, 0] == m) & (pairs[:, 1] == m + 1)].tolist() == [2] * 3000
+    assert set(rc[(pairs[:, 0] == m) & (pairs[:, 1] == m + 1)].tolist()) == {m}
+    ix = gpu_index(pspc, g, rank)
+    assert ix.label_sizes([m, m + 1]).min() >= m
+    for lanes in (pspc.PSPC_QUERY_BY_SOURCE, pspc.PSPC_QUERY_BY_SOURCE_HASH, 256, 8, 0):
+        ix.set_query_group(lanes)
+        d, c, f = gpu_query(ix, pairs)
+        assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
+    ix.free()
 
 
 def test_by_source_skew_repeats_and_overflow(pspc):
@@ -291,7 +337,7 @@ def test_by_source_skew_repeats_and_overflow(pspc):
         pairs = pairs[rng.permutation(len(pairs))]
         rd, rc, rf, _ = oracle.OracleIndex(gg, rk).query(pairs)
         ix = gpu_index(pspc, gg, rk)
-        for lanes in (pspc.PSPC_QUERY_BY_SOURCE, 256, 8):
+        for lanes in (pspc.PSPC_QUERY_BY_SOURCE, pspc.PSPC_QUERY_BY_SOURCE_HASH, 256, 8):
             ix.set_query_group(lanes)
             d, c, f = gpu_query(ix, pairs)
             assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
@@ -299,12 +345,16 @@ def test_by_source_skew_repeats_and_overflow(pspc):
             assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
         if gg is dg:
             assert rf.any()
-        bad = pairs.copy()
-        bad[len(bad) // 2, 0] = gg.n
-        with pytest.raises(pspc.PSPCError) as e:
-            ix.set_query_group(0)
-            gpu_query(ix, bad)
-        assert e.value.code == 1
+        for lanes in (pspc.PSPC_QUERY_BY_SOURCE, pspc.PSPC_QUERY_BY_SOURCE_HASH, 0):
+            ix.set_query_group(lanes)
+            for bad_pair in ((gg.n, 0), (-1, 3), (3, gg.n), (7, -5)):
+                bad = pairs.copy()
+                bad[len(bad) // 2] = bad_pair
+                with pytest.raises(pspc.PSPCError) as e:
+                    gpu_query(ix, bad)
+                assert e.value.code == 1, (lanes, bad_pair)
+            d, c, f = gpu_query(ix, pairs)  # the index still answers
+            assert np.array_equal(d, rd) and np.array_equal(c, rc) and np.array_equal(f, rf), lanes
         ix.free()
 
 
