@@ -353,16 +353,27 @@ int pspc_query_noalloc(const pspc_index* ix, const int32_t* pairs, int64_t q, ui
                        uint64_t* count, uint8_t* overflow, void* stream);
 
 /*
- * pspc_landmarks -- the landmark distances the build used for its landmark
- * filter (Section "Landmark-Based Filtering"; the landmarks of a graph are
- * its k highest-ranked vertices, k = pspc_opts.landmarks).
- * k:    host int32 out; the landmarks per graph (0 when the filter was off).
- * dist: NULL, or host uint16[n][k] out by caller vertex id: dist[v*k + j] =
- *       sd(v, j-th highest-ranked vertex of v's graph), or 0xFFFF when the
- *       two are not connected or v's graph has no j-th vertex.
- * Errors: PSPC_E_INVAL (NULL index or k), PSPC_E_NOMEM, PSPC_E_CUDA.
+ * pspc_landmarks -- the landmarks and landmark distances the build used for
+ * its landmark filter (Section "Landmark-Based Filtering"). Landmarks
+ * 0 .. min(k, 32)-1 of a graph are its highest-ranked vertices, the
+ * paper's degree threshold under a degree order. For an index of one graph
+ * with k > 32 and more than 4k vertices, landmarks 32 .. k-1 are spread
+ * over the graph instead (the filter tests them from level 16 on, where
+ * they prove most survivors of high-diameter graphs): each in turn is the
+ * vertex that maximises the smaller of its distance to landmarks 0..31 and
+ * the landmark lower bound max_j |sd(v,l_j) - sd(p,l_j)|, j < 32, of its
+ * distance to every spread landmark p before it, ties to the smaller id.
+ * k:      host int32 out; the landmarks per graph (0 when the filter was
+ *         off).
+ * dist:   NULL, or host uint16[n][k] out by caller vertex id:
+ *         dist[v*k + j] = sd(v, landmark j of v's graph), or 0xFFFF when
+ *         the two are not connected or v's graph has no landmark j.
+ * vertex: NULL, or host int32[k] out for an index of one graph: the caller
+ *         id of landmark j (-1: none).
+ * Errors: PSPC_E_INVAL (NULL index or k, vertex for a batch or 1-shell
+ * index), PSPC_E_NOMEM, PSPC_E_CUDA.
  */
-int pspc_landmarks(const pspc_index* ix, int32_t* k, uint16_t* dist);
+int pspc_landmarks(const pspc_index* ix, int32_t* k, uint16_t* dist, int32_t* vertex);
 
 /*
  * pspc_inject_alloc_failure -- fault injection for tests of the library's

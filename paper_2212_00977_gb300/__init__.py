@@ -90,7 +90,7 @@ _SIGS = {
     "pspc_export_vertices": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     "pspc_hub_column": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "pspc_query_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
-    "pspc_landmarks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), _P]),
+    "pspc_landmarks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), _P, _P]),
     "pspc_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32]),
     "pspc_free": (None, [_P]),
     "pspc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -281,16 +281,31 @@ class Index:
 
     def landmarks(self) -> np.ndarray:
         """pspc_landmarks: uint16 [n, k] distances from each vertex to the k
-        highest-ranked vertices of its graph (0xFFFF = unreached or none);
-        k = 0 when the build ran without the landmark filter."""
+        landmarks of its graph (0xFFFF = unreached or none); k = 0 when the
+        build ran without the landmark filter."""
         lib = load()
         k = ctypes.c_int32()
-        rc = lib.pspc_landmarks(self._h, ctypes.byref(k), None)
+        rc = lib.pspc_landmarks(self._h, ctypes.byref(k), None, None)
         if rc != PSPC_OK:
             raise PSPCError(rc, "pspc_landmarks")
         out = np.empty((self.n, k.value), dtype=np.uint16)
         if k.value:
-            rc = lib.pspc_landmarks(self._h, ctypes.byref(k), _ptr(out))
+            rc = lib.pspc_landmarks(self._h, ctypes.byref(k), _ptr(out), None)
+            if rc != PSPC_OK:
+                raise PSPCError(rc, "pspc_landmarks")
+        return out
+
+    def landmark_vertices(self) -> np.ndarray:
+        """pspc_landmarks: int32 [k] caller ids of the landmarks of a
+        one-graph index (-1: none)."""
+        lib = load()
+        k = ctypes.c_int32()
+        rc = lib.pspc_landmarks(self._h, ctypes.byref(k), None, None)
+        if rc != PSPC_OK:
+            raise PSPCError(rc, "pspc_landmarks")
+        out = np.full(k.value, -1, dtype=np.int32)
+        if k.value:
+            rc = lib.pspc_landmarks(self._h, ctypes.byref(k), None, _ptr(out))
             if rc != PSPC_OK:
                 raise PSPCError(rc, "pspc_landmarks")
         return out

@@ -1074,8 +1074,9 @@ struct Builder {
     }
 
     // Landmark labelling (Section "Landmark-Based Filtering"): distances
-    // from the o.landmarks highest-ranked vertices of every graph, kept with
-    // the index.
+    // from o.landmarks landmarks per graph (the highest-ranked vertices;
+    // past the first kLmkShallow, spread ones for a large single graph),
+    // kept with the index.
     int landmarks() {
         out.lmk_k = o.landmarks;
         out.lmk_stride = (2 * o.landmarks + 15) / 16 * 16;
@@ -1084,7 +1085,8 @@ struct Builder {
         PSPC_TRY_CUDA(cudaEventCreate(&a));
         PSPC_TRY_CUDA(cudaEventCreate(&b));
         cudaEventRecord(a, st);
-        int rc = landmark_bfs(n, rp_r, col_r, comp_base, out.lmk_k, out.lmk_stride, out.lmk, st, &out.launches);
+        int rc = landmark_bfs(n, rp_r, col_r, comp_base, out.lmk_k, out.lmk_stride, out.lmk, out.lmk_ids, st,
+                              &out.launches);
         cudaEventRecord(b, st);
         if (!rc) {
             cudaEventSynchronize(b);
@@ -1512,6 +1514,7 @@ static int build_reduced(const pspc_csr* g, const int32_t* rank, const pspc_opts
         ix.launches = B.out.launches + c.launches;
         ix.lstats = c.lstats;
         ix.lmk_k = c.lmk ? c.lmk_k : 0;
+        memcpy(ix.lmk_ids, c.lmk_ids, sizeof(ix.lmk_ids));
         ix.lmk_ms = c.lmk_ms;
         cudaEventElapsedTime(&ix.build_ms, t0, t1);
         ix.core = core;

@@ -61,6 +61,7 @@ struct Index {
     uint8_t* lmk = nullptr;   // [n][lmk_stride] bytes: uint16 landmark distances (rank ids), or NULL
     int32_t lmk_k = 0;        // landmarks per graph
     int32_t lmk_stride = 0;   // bytes per row (2 * lmk_k rounded up to 16)
+    int32_t lmk_ids[64] = {};  // id (rank) of landmark j of a one-graph index, -1 for none
     float lmk_ms = 0.f;       // device time of the landmark BFS
     // 1-shell reduction: when `core` is set, the labels are those of the
     // 2-core, held by `core` (an index over core ids), and every vertex of G

@@ -1,15 +1,29 @@
 // Landmark labelling for the landmark filter of pruning rule 2 (Section
-// "Landmark-Based Filtering"). The landmarks of a graph are its k
-// highest-ranked vertices; under a degree order these are the vertices whose
-// degree reaches the k-th largest degree, the paper's degree threshold. The
-// filter needs sd(v, l) for every vertex v and landmark l: all k
-// breadth-first searches run together, one BFS level per launch. Every
-// vertex keeps a 64-bit mask of the landmarks that have reached it; at level
-// t it takes the OR of its neighbours' frontier masks, and the bits new to it
-// get distance t.
+// "Landmark-Based Filtering"). The first landmarks of a graph (up to
+// kLmkShallow) are its highest-ranked vertices; under a degree order these
+// are the vertices whose degree reaches the k-th largest degree, the
+// paper's degree threshold. The filter needs sd(v, l) for every vertex v and
+// landmark l: the searches of a round run together, one BFS level per
+// launch. Every vertex keeps a 64-bit mask of the round's landmarks that
+// have reached it; at level t it takes the OR of its neighbours' frontier
+// masks, and the bits new to it get distance t.
+//
+// The remaining landmarks of a single graph (k > kLmkShallow; the filter
+// tests them from level kLmkDeepLevel on) are spread out instead: a
+// survivor h of u at level d is proven by landmark l when
+// |sd(u,l) - sd(h,l)| >= d, that is when l lies behind h on a shortest path
+// from u (or behind u), and for far-apart u and h that region is near the
+// graph's periphery, where high-ranked vertices of a high-diameter graph
+// seldom lie. Each spread landmark, chosen in turn, maximises over the
+// vertices reached in the first round the smaller of (a) its distance to
+// the first round's landmarks and (b) the landmark lower bound
+// max_j |sd(v,l_j) - sd(p,l_j)| of its distance to every spread landmark p
+// chosen before it (ties to the smaller id), so it is far from all of
+// them; a second round of searches gives their distances.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "pspc_level.cuh"
@@ -39,10 +53,10 @@ __global__ void k_lmk_init(int64_t n, int k, int stride, const int32_t* __restri
     if (is_lmk) lmk_row(ld, v, stride)[j] = 0;
 }
 
-// One BFS level for all landmarks: kLmkGroup lanes per vertex OR the
-// frontier masks of its neighbours.
+// One BFS level for all landmarks of a round: kLmkGroup lanes per vertex OR
+// the frontier masks of its neighbours; bit j is landmark slot slot0 + j.
 __global__ void __launch_bounds__(kLmkThreads)
-    k_lmk_level(int64_t n, int stride, int level, uint64_t full, const int64_t* __restrict__ rp,
+    k_lmk_level(int64_t n, int stride, int level, uint64_t full, int slot0, const int64_t* __restrict__ rp,
                 const int32_t* __restrict__ col, const uint64_t* __restrict__ frontier, uint64_t* __restrict__ next,
                 uint64_t* __restrict__ visited, uint8_t* __restrict__ ld, int* __restrict__ changed) {
     const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kLmkGroup;
@@ -65,42 +79,149 @@ __global__ void __launch_bounds__(kLmkThreads)
         }
     }
     for (int j = gl; j < 64; j += kLmkGroup)
-        if ((fresh >> j) & 1ull) lmk_row(ld, v, stride)[j] = (uint16_t)level;
+        if ((fresh >> j) & 1ull) lmk_row(ld, v, stride)[slot0 + j] = (uint16_t)level;
+}
+
+// Spread landmarks. cur[v]: the score of v (the smaller of its distance to
+// the first round's k1 landmarks and its lower bounds to the spread ones
+// chosen so far); 0 for vertices no first-round landmark reached.
+__global__ void k_lmk_score(int64_t n, int stride, int k1, const uint8_t* __restrict__ ld, uint32_t* __restrict__ cur) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const uint16_t* r = (const uint16_t*)(ld + v * stride);
+    uint32_t m = 0xFFFFFFFFu;
+    for (int j = 0; j < k1; ++j)
+        if (r[j] != 0xFFFFu) m = min(m, (uint32_t)r[j]);
+    cur[v] = m == 0xFFFFFFFFu ? 0u : m;
+}
+
+// The largest score, ties to the smaller id: key = score << 32 | ~v.
+__global__ void k_lmk_argmax(int64_t n, const uint32_t* __restrict__ cur, unsigned long long* __restrict__ key) {
+    unsigned long long best = 0ull;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        best = max(best, (unsigned long long)cur[v] << 32 | (0xFFFFFFFFull - (unsigned long long)v));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(key, best);
+}
+
+// Takes the chosen vertex p as spread landmark `slot` (ids[slot]) and
+// lowers every score to the landmark lower bound of sd(v, p) (0xFFFF when
+// exactly one of v, p was reached by some first-round landmark: they are
+// not connected).
+__global__ void k_lmk_take(int64_t n, int stride, int k1, const uint8_t* __restrict__ ld, uint32_t* __restrict__ cur,
+                           const unsigned long long* __restrict__ key, int32_t* __restrict__ ids, int slot) {
+    const int64_t p = (int64_t)(0xFFFFFFFFull - (*key & 0xFFFFFFFFull));
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v == 0) ids[slot] = (int32_t)p;
+    if (v >= n || p >= n) return;
+    const uint16_t* rv = (const uint16_t*)(ld + v * stride);
+    const uint16_t* rp = (const uint16_t*)(ld + p * stride);
+    uint32_t lb = 0;
+    for (int j = 0; j < k1; ++j) {
+        const uint32_t a = rv[j], b = rp[j];
+        if (a == 0xFFFFu && b == 0xFFFFu) continue;
+        if (a == 0xFFFFu || b == 0xFFFFu) {
+            lb = 0xFFFFu;
+            break;
+        }
+        lb = max(lb, a > b ? a - b : b - a);
+    }
+    cur[v] = min(cur[v], lb);
+}
+
+// Second-round sources: spread landmark j (slot k1 + j) at vertex ids[k1 + j].
+__global__ void k_lmk_seed(int64_t n, int count, int k1, int stride, const int32_t* __restrict__ ids,
+                           uint64_t* __restrict__ visited,
+                           uint64_t* __restrict__ frontier, uint8_t* __restrict__ ld) {
+    const int j = threadIdx.x;
+    if (j >= count) return;
+    const int64_t v = ids[k1 + j];
+    if (v < 0 || v >= n) return;  // no vertex was chosen (not reached for n > 0)
+    atomicOr((unsigned long long*)&visited[v], 1ull << j);
+    atomicOr((unsigned long long*)&frontier[v], 1ull << j);
+    lmk_row(ld, v, stride)[k1 + j] = 0;
+}
+
+// The searches of one round: bits of `full` from the round's sources
+// (already set in visited and fa), distances into slots slot0 + j.
+static cudaError_t lmk_round(int64_t n, const int64_t* rp, const int32_t* col, int stride, uint64_t full, int slot0,
+                             uint8_t* ld, uint64_t* visited, uint64_t* fa, uint64_t* fb, int* changed, cudaStream_t st,
+                             int64_t* nl) {
+    cudaError_t e = cudaSuccess;
+    const unsigned blocks = (unsigned)((n * kLmkGroup + kLmkThreads - 1) / kLmkThreads);
+    for (int level = 1; level <= kLmkMaxDist;) {
+        if ((e = cudaMemsetAsync(changed, 0, sizeof(int), st)) != cudaSuccess) return e;
+        // A level after the last one that reaches anything changes nothing,
+        // so a few levels run between host checks.
+        for (int t = 0; t < kLmkLevelsPerCheck && level <= kLmkMaxDist; ++t, ++level) {
+            k_lmk_level<<<blocks, kLmkThreads, 0, st>>>(n, stride, level, full, slot0, rp, col, fa, fb, visited, ld,
+                                                        changed);
+            std::swap(fa, fb);
+            ++*nl;
+        }
+        int h = 0;
+        if ((e = cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        if (!h) break;
+    }
+    return cudaGetLastError();
 }
 
 int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* comp_base, int k, int stride,
-                 uint8_t* ld, cudaStream_t st, int64_t* launches) {
+                 uint8_t* ld, int32_t* ids, cudaStream_t st, int64_t* launches) {
     if (k < 1 || k > 64 || stride % 16 || stride < 2 * k) return PSPC_E_INVAL;
+    // spread landmarks only for one graph large enough to place them
+    const int k1 = (comp_base || k <= kLmkShallow || n <= 4 * (int64_t)k) ? k : kLmkShallow;
+    const int k2 = k - k1;
     void* mem = nullptr;
     const size_t masks = (size_t)n * 8;
-    cudaError_t e = dev_alloc(&mem, 3 * masks + 256, st);
+    cudaError_t e = dev_alloc(&mem, 3 * masks + (size_t)n * 4 + 64 * 8 + 64 * 4 + 256, st);
     if (e != cudaSuccess) return cuda_status(e);
     uint64_t* visited = (uint64_t*)mem;
     uint64_t* fa = visited + n;
     uint64_t* fb = fa + n;
-    int* changed = (int*)(fb + n);
-    const uint64_t full = k == 64 ? ~0ull : ((1ull << k) - 1);
-    int rc = PSPC_OK;
-    k_lmk_init<<<(unsigned)((n + kLmkThreads - 1) / kLmkThreads), kLmkThreads, 0, st>>>(n, k, stride, comp_base,
-                                                                                         visited, fa, ld);
+    unsigned long long* keys = (unsigned long long*)(fb + n);
+    int32_t* d_ids = (int32_t*)(keys + 64);
+    uint32_t* cur = (uint32_t*)(d_ids + 64);
+    int* changed = (int*)(cur + n);
     int64_t nl = 1;
-    const unsigned blocks = (unsigned)((n * kLmkGroup + kLmkThreads - 1) / kLmkThreads);
-    for (int level = 1; level <= kLmkMaxDist && rc == PSPC_OK;) {
-        if ((e = cudaMemsetAsync(changed, 0, sizeof(int), st)) != cudaSuccess) break;
-        // A level after the last one that reaches anything changes nothing,
-        // so a few levels run between host checks.
-        for (int t = 0; t < kLmkLevelsPerCheck && level <= kLmkMaxDist; ++t, ++level) {
-            k_lmk_level<<<blocks, kLmkThreads, 0, st>>>(n, stride, level, full, rp, col, fa, fb, visited, ld, changed);
-            std::swap(fa, fb);
-            ++nl;
+    const unsigned vb = (unsigned)((n + kLmkThreads - 1) / kLmkThreads);
+    k_lmk_init<<<vb, kLmkThreads, 0, st>>>(n, k1, stride, comp_base, visited, fa, ld);
+    e = lmk_round(n, rp, col, stride, k1 == 64 ? ~0ull : ((1ull << k1) - 1), 0, ld, visited, fa, fb, changed, st, &nl);
+    if (e == cudaSuccess && k2 > 0) {
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned ab = (unsigned)std::min<int64_t>(vb, std::max(sms, 1) * 4);
+        if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, 64 * 8, st);
+        if (e == cudaSuccess) {
+            k_lmk_score<<<vb, kLmkThreads, 0, st>>>(n, stride, k1, ld, cur);
+            nl += 1;
+            for (int j = 0; j < k2; ++j) {
+                k_lmk_argmax<<<ab, kLmkThreads, 0, st>>>(n, cur, keys + j);
+                k_lmk_take<<<vb, kLmkThreads, 0, st>>>(n, stride, k1, ld, cur, keys + j, d_ids, k1 + j);
+                nl += 2;
+            }
+            e = cudaGetLastError();
         }
-        int h = 0;
-        if ((e = cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
-        if (!h) break;
+        if (e == cudaSuccess) e = cudaMemsetAsync(visited, 0, 2 * masks, st);
+        if (e == cudaSuccess) {
+            k_lmk_seed<<<1, 64, 0, st>>>(n, k2, k1, stride, d_ids, visited, fa, ld);
+            nl += 1;
+            e = lmk_round(n, rp, col, stride, k2 == 64 ? ~0ull : ((1ull << k2) - 1), k1, ld, visited, fa, fb, changed,
+                          st, &nl);
+        }
+    }
+    if (e == cudaSuccess && ids) {
+        for (int j = 0; j < 64; ++j) ids[j] = j < k1 && j < n ? j : -1;
+        if (k2 > 0) {
+            e = cudaMemcpyAsync(ids + k1, d_ids + k1, (size_t)k2 * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
     }
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) rc = cuda_status(e);
+    const int rc = e == cudaSuccess ? PSPC_OK : cuda_status(e);
     dev_free(mem, st);
     if (launches) *launches += nl;
     return rc;

@@ -143,14 +143,17 @@ __host__ __device__ inline size_t level_map_bytes(int kind, int d, uint32_t bm_w
     return kind == kMapBitmap ? bitmap_bytes(d, bm_words) : kind == kMapHash ? hashmap_bytes(cap_u) : 0;
 }
 
-// Landmark labelling (pspc_landmark.cu): exact BFS distances from the k
-// highest-ranked vertices of every graph (rank-space ids comp_base[v] + j,
-// or j when comp_base is NULL), all k searches at once with one 64-bit mask
-// of reached landmarks per vertex. ld is [n][stride] bytes, k uint16
-// distances per row, 0xFFFF where the distance is undefined (unreached, or
-// no such landmark). Synchronises st every few BFS levels.
+// Landmark distances (Section "Landmark-Based Filtering"): the first
+// min(k, kLmkShallow) landmarks of every graph are its highest-ranked
+// vertices (id comp_base + j, or j when comp_base is NULL); for one graph
+// (comp_base NULL) with k > kLmkShallow and more than 4k vertices the others
+// are spread out over the graph (chosen one by one, each far from the
+// landmarks before it). ld is [n][stride] bytes, k uint16 distances per
+// row, 0xFFFF where the distance is undefined (unreached, or no such
+// landmark). ids (NULL, or host int32[64] out): the id of landmark j, -1 for
+// none. Synchronises st every few BFS levels.
 int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* comp_base, int k, int stride,
-                 uint8_t* ld, cudaStream_t st, int64_t* launches);
+                 uint8_t* ld, int32_t* ids, cudaStream_t st, int64_t* launches);
 
 // Push paradigm (Algorithm PUSH): every arc u->v sends u the entries of
 // L_{d-1}(v) that the pull would read for it (cnt_arc[a] of them from

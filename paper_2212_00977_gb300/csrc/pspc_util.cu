@@ -248,11 +248,11 @@ extern "C" int pspc_stats(const pspc_index* h, pspc_stats_t* s) {
     return PSPC_OK;
 }
 
-extern "C" int pspc_landmarks(const pspc_index* h, int32_t* k, uint16_t* dist) {
-    if (!h || !k || h->ix.core) return PSPC_E_INVAL;
+extern "C" int pspc_landmarks(const pspc_index* h, int32_t* k, uint16_t* dist, int32_t* vertex) {
+    if (!h || !k || h->ix.core || (vertex && h->ix.graphs != 1)) return PSPC_E_INVAL;
     const Index& ix = h->ix;
     *k = ix.lmk ? ix.lmk_k : 0;
-    if (!dist || !ix.lmk) return PSPC_OK;
+    if ((!dist && !vertex) || !ix.lmk) return PSPC_OK;
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ix.device);
@@ -270,8 +270,14 @@ extern "C" int pspc_landmarks(const pspc_index* h, int32_t* k, uint16_t* dist) {
     if (!rc) e = cudaMemcpy(rows.data(), ix.lmk, rows.size(), cudaMemcpyDeviceToHost);
     if (!rc && e == cudaSuccess) e = cudaMemcpy(rank.data(), ix.rank, (size_t)ix.n * 4, cudaMemcpyDeviceToHost);
     if (!rc && e != cudaSuccess) rc = cuda_status(e);
-    if (!rc)
+    if (!rc && dist)
         for (int64_t v = 0; v < ix.n; ++v) memcpy(dist + (size_t)v * K, rows.data() + (size_t)rank[v] * S, 2 * K);
+    if (!rc && vertex) {
+        for (size_t j = 0; j < K; ++j) vertex[j] = -1;
+        for (int64_t v = 0; v < ix.n; ++v)  // caller id of each landmark's rank
+            for (size_t j = 0; j < K; ++j)
+                if (ix.lmk_ids[j] == rank[v]) vertex[j] = (int32_t)v;
+    }
     cudaSetDevice(prev);
     return rc;
 }

@@ -46,6 +46,18 @@ def bipartite_2m(m: int) -> Graph:
     return csr_from_edges(m + 2, np.array(e), f"K2,{m}")
 
 
+def hub_ladder(m: int, depth: int) -> Graph:
+    """m hubs 0..m-1, each joined to both vertices of layer 1 of a ladder of
+    width 2 and the given depth (vertices m + 2(k-1), m + 2(k-1) + 1 in
+    layer k; consecutive layers completely joined). A hub reaches a layer-k
+    vertex by 2^(k-1) shortest paths of length k."""
+    e = [(z, m + i) for z in range(m) for i in range(2)]
+    for k in range(1, depth):
+        a, b = m + 2 * (k - 1), m + 2 * k
+        e += [(a + i, b + j) for i in range(2) for j in range(2)]
+    return csr_from_edges(m + 2 * depth, np.array(e), f"hubladder{m}x{depth}")
+
+
 def hypercube(k: int) -> Graph:
     n = 1 << k
     e = [(v, v ^ (1 << b)) for v in range(n) for b in range(k) if v < v ^ (1 << b)]

@@ -115,6 +115,26 @@ def test_diamond_chain_label_overflow(pspc, k):
     assert (int(ref.ovf.sum()) > 0) == (k >= 64)
 
 
+def test_offchip_counts_carry_past_2_64(pspc):
+    """500 hubs over a width-2 ladder 66 layers deep: every ladder vertex
+    pulls 1000 entries for 500 hubs, more than an on-chip table of 1024 slots
+    holds, so with cand_capacity=1024 the level runs off chip; at layer 65
+    each hub's count is 2^63 + 2^63 (a carry past 2^64 in the split sums),
+    at 66 the pulled entries already carry the flag. The index equals the
+    oracle's with every map kind and in the default configuration."""
+    g = G.hub_ladder(500, 66)
+    rank = np.arange(g.n, dtype=np.int32)
+    ref = oracle.OracleIndex(g, rank).export()
+    assert ref.ovf.sum() > 0
+    for kw in (dict(), dict(cand_capacity=1024), dict(cand_capacity=1024, map_kind=2, label_capacity=1024),
+               dict(cand_capacity=1024, map_kind=3), dict(cand_capacity=1024, paradigm=1)):
+        ix = gpu_index(pspc, g, rank, **kw)
+        assert_index_equal(ix, ref)
+        if kw:
+            assert sum(l["offchip_vertices"] for l in ix.level_stats()) >= 2 * 60, kw
+        ix.free()
+
+
 def test_trees_isolated_components_and_tiny(pspc):
     for g, rank in [
         (G.random_tree(300, 1), G.random_rank(300, 1)),
