@@ -97,15 +97,21 @@ typedef struct {
                                 batch next to a build) gets SMs as soon as
                                 any vertex finishes; same results */
     int32_t landmarks;       /* landmark filter of pruning rule 2 (Section
-                                "Landmark-Based Filtering"): the K highest-
-                                ranked vertices of every graph are
-                                landmarks, and their exact BFS distances to
-                                every vertex (two bytes each) let the prune
-                                step drop a candidate h of u at level d at
-                                once when sd(u,l) + sd(l,h) < d for some
-                                landmark l. 0 = default (K = 64), -1 = off,
-                                1..64 = K; levels below 16 test at most
-                                the first 32. Results do not depend on it */
+                                "Landmark-Based Filtering"): K landmarks
+                                per graph, the highest-ranked vertices
+                                (past the first 32 of a single large
+                                graph, spread ones: see pspc_landmarks);
+                                their exact BFS distances to every vertex
+                                (two bytes each) let the prune step drop a
+                                candidate h of u at level d at once when
+                                sd(u,l) + sd(l,h) < d for some landmark l,
+                                and keep it unscanned when
+                                |sd(u,l) - sd(l,h)| >= d. 0 = default
+                                (K = 128; 64 in pspc_build_batch), -1 =
+                                off, 1..128 = K (at most 64 in
+                                pspc_build_batch); levels below 16 test at
+                                most the first 32. Results do not depend
+                                on it */
     int32_t reduce_shell;    /* 1: reduction by 1-shell (Section "Index
                                 Size Reduction"): vertices of degree 1 are
                                 peeled repeatedly, the index is built on the

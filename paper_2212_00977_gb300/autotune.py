@@ -12,7 +12,7 @@ import math
 
 QUERY_VARIANTS = (1, 16, 32, 64, 128, 256)  # 1 = by source (pspc.PSPC_QUERY_BY_SOURCE)
 BUILD_VARIANTS = tuple(dict(cand_capacity=c, map_kind=m) for c in (2048, 4096, 8192) for m in (0, 2, 3))
-LANDMARK_VARIANTS = (-1, 16, 32, 64)  # second stage: landmark count on top of the best tables
+LANDMARK_VARIANTS = (-1, 32, 64, 128)  # second stage: landmark count on top of the best tables
 
 _cache: dict = {}
 

@@ -1389,18 +1389,20 @@ struct Builder {
 
 using namespace pspc;
 
-static void fill_defaults(pspc_opts& o, const pspc_opts* user) {
+// Default landmarks: 128 for one graph (32 highest-ranked and 96 spread),
+// 64 highest-ranked per graph in a batch (one BFS round).
+static void fill_defaults(pspc_opts& o, const pspc_opts* user, bool batch = false) {
     memset(&o, 0, sizeof(o));
     if (user) o = *user;
     if (o.cand_capacity <= 0) o.cand_capacity = 4096;
     if (o.label_capacity <= 0) o.label_capacity = 8192;
     if (o.max_levels <= 0) o.max_levels = kMaxDist;
-    if (o.landmarks == 0) o.landmarks = 64;
+    if (o.landmarks == 0) o.landmarks = batch ? 64 : kLmkMax;
 }
 
 static bool opts_ok(const pspc_opts& o) {
     return o.map_kind >= 0 && o.map_kind <= 3 && o.max_ctas >= 0 && (o.granular == 0 || o.granular == 1) &&
-           o.landmarks >= -1 && o.landmarks <= 64 && (o.paradigm == 0 || o.paradigm == 1) && o.warp_levels >= -1;
+           o.landmarks >= -1 && o.landmarks <= kLmkMax && (o.paradigm == 0 || o.paradigm == 1) && o.warp_levels >= -1;
 }
 
 static bool pow2_in(int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
@@ -1408,10 +1410,11 @@ static bool pow2_in(int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= 
 // Common driver: stage the input (one graph or a batch), check it, relabel,
 // build the levels, finalize, and hand the index to the caller.
 template <typename Stage>
-static int run_build(const pspc_opts* opts, pspc_index** out, void* stream, int32_t graphs, Stage stage) {
+static int run_build(const pspc_opts* opts, pspc_index** out, void* stream, int32_t graphs, Stage stage,
+                     bool batch = false) {
     Builder B;
     B.st = (cudaStream_t)stream;
-    fill_defaults(B.o, opts);
+    fill_defaults(B.o, opts, batch);
     if (!pow2_in(B.o.cand_capacity, 1024, 16384) || !pow2_in(B.o.label_capacity, 1024, 16384) || !opts_ok(B.o))
         return PSPC_E_INVAL;
     PSPC_TRY_CUDA(cudaGetDevice(&B.dev));
@@ -1547,6 +1550,7 @@ extern "C" int pspc_build_batch(const pspc_graph* graphs, int32_t k, const pspc_
                                 void* stream) {
     if (!out) return PSPC_E_INVAL;
     *out = nullptr;
-    if (!graphs || k < 1 || (opts && opts->reduce_shell)) return PSPC_E_INVAL;
-    return run_build(opts, out, stream, k, [&](Builder& B) { return B.stage_batch(graphs, k); });
+    // a batch keeps one BFS round of landmarks: at most 64 per graph
+    if (!graphs || k < 1 || (opts && (opts->reduce_shell || opts->landmarks > 64))) return PSPC_E_INVAL;
+    return run_build(opts, out, stream, k, [&](Builder& B) { return B.stage_batch(graphs, k); }, true);
 }

@@ -20,6 +20,7 @@ constexpr uint32_t kHubMask = 0x00FFFFFFu;
 constexpr uint32_t kOvfBit = 0x80000000u;   // overflow flag carried with a hub word
 constexpr uint32_t kMarkBit = 0x40000000u;  // survivor mark inside candidate tables
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;    // empty hash slot
+constexpr int kLmkMax = 128;               // landmarks per graph at most (64 in a batch of graphs)
 constexpr int64_t kMaxVertices = (1 << 24) - 1;
 constexpr int kMaxDist = 32767;
 
@@ -61,7 +62,7 @@ struct Index {
     uint8_t* lmk = nullptr;   // [n][lmk_stride] bytes: uint16 landmark distances (rank ids), or NULL
     int32_t lmk_k = 0;        // landmarks per graph
     int32_t lmk_stride = 0;   // bytes per row (2 * lmk_k rounded up to 16)
-    int32_t lmk_ids[64] = {};  // id (rank) of landmark j of a one-graph index, -1 for none
+    int32_t lmk_ids[kLmkMax] = {};  // id (rank) of landmark j of a one-graph index, -1 for none
     float lmk_ms = 0.f;       // device time of the landmark BFS
     // 1-shell reduction: when `core` is set, the labels are those of the
     // 2-core, held by `core` (an index over core ids), and every vertex of G

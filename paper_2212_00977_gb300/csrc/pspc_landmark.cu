@@ -130,17 +130,17 @@ __global__ void k_lmk_take(int64_t n, int stride, int k1, const uint8_t* __restr
     cur[v] = min(cur[v], lb);
 }
 
-// Second-round sources: spread landmark j (slot k1 + j) at vertex ids[k1 + j].
-__global__ void k_lmk_seed(int64_t n, int count, int k1, int stride, const int32_t* __restrict__ ids,
-                           uint64_t* __restrict__ visited,
-                           uint64_t* __restrict__ frontier, uint8_t* __restrict__ ld) {
+// Sources of a later round: landmark slot s0 + j at vertex ids[s0 + j]
+// (none for -1).
+__global__ void k_lmk_seed(int64_t n, int s0, int count, int stride, const int32_t* __restrict__ ids,
+                           uint64_t* __restrict__ visited, uint64_t* __restrict__ frontier, uint8_t* __restrict__ ld) {
     const int j = threadIdx.x;
     if (j >= count) return;
-    const int64_t v = ids[k1 + j];
-    if (v < 0 || v >= n) return;  // no vertex was chosen (not reached for n > 0)
+    const int64_t v = ids[s0 + j];
+    if (v < 0 || v >= n) return;
     atomicOr((unsigned long long*)&visited[v], 1ull << j);
     atomicOr((unsigned long long*)&frontier[v], 1ull << j);
-    lmk_row(ld, v, stride)[k1 + j] = 0;
+    lmk_row(ld, v, stride)[s0 + j] = 0;
 }
 
 // The searches of one round: bits of `full` from the round's sources
@@ -170,55 +170,65 @@ static cudaError_t lmk_round(int64_t n, const int64_t* rp, const int32_t* col, i
 
 int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* comp_base, int k, int stride,
                  uint8_t* ld, int32_t* ids, cudaStream_t st, int64_t* launches) {
-    if (k < 1 || k > 64 || stride % 16 || stride < 2 * k) return PSPC_E_INVAL;
-    // spread landmarks only for one graph large enough to place them
+    if (k < 1 || k > kLmkMax || (comp_base && k > 64) || stride % 16 || stride < 2 * k) return PSPC_E_INVAL;
+    // slots 0..k1-1: the highest-ranked vertices; k1..k-1: spread landmarks,
+    // only for one graph large enough to place them
     const int k1 = (comp_base || k <= kLmkShallow || n <= 4 * (int64_t)k) ? k : kLmkShallow;
-    const int k2 = k - k1;
     void* mem = nullptr;
     const size_t masks = (size_t)n * 8;
-    cudaError_t e = dev_alloc(&mem, 3 * masks + (size_t)n * 4 + 64 * 8 + 64 * 4 + 256, st);
+    cudaError_t e = dev_alloc(&mem, 3 * masks + (size_t)n * 4 + kLmkMax * 12 + 256, st);
     if (e != cudaSuccess) return cuda_status(e);
     uint64_t* visited = (uint64_t*)mem;
     uint64_t* fa = visited + n;
     uint64_t* fb = fa + n;
     unsigned long long* keys = (unsigned long long*)(fb + n);
-    int32_t* d_ids = (int32_t*)(keys + 64);
-    uint32_t* cur = (uint32_t*)(d_ids + 64);
+    int32_t* d_ids = (int32_t*)(keys + kLmkMax);
+    uint32_t* cur = (uint32_t*)(d_ids + kLmkMax);
     int* changed = (int*)(cur + n);
+    int32_t h_ids[kLmkMax];
+    for (int j = 0; j < kLmkMax; ++j) h_ids[j] = j < k1 && j < n ? j : -1;
     int64_t nl = 1;
     const unsigned vb = (unsigned)((n + kLmkThreads - 1) / kLmkThreads);
-    k_lmk_init<<<vb, kLmkThreads, 0, st>>>(n, k1, stride, comp_base, visited, fa, ld);
-    e = lmk_round(n, rp, col, stride, k1 == 64 ? ~0ull : ((1ull << k1) - 1), 0, ld, visited, fa, fb, changed, st, &nl);
-    if (e == cudaSuccess && k2 > 0) {
+    // round 1: the first (up to 64) highest-ranked vertices of every graph
+    const int r1 = k1 < 64 ? k1 : 64;
+    k_lmk_init<<<vb, kLmkThreads, 0, st>>>(n, r1, stride, comp_base, visited, fa, ld);
+    e = cudaMemcpyAsync(d_ids, h_ids, sizeof(h_ids), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = lmk_round(n, rp, col, stride, r1 == 64 ? ~0ull : ((1ull << r1) - 1), 0, ld, visited, fa, fb, changed, st,
+                      &nl);
+    if (e == cudaSuccess && k1 < k) {  // spread landmarks, from the first round's distances (k1 <= 64)
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const unsigned ab = (unsigned)std::min<int64_t>(vb, std::max(sms, 1) * 4);
-        if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, 64 * 8, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, kLmkMax * 8, st);
         if (e == cudaSuccess) {
             k_lmk_score<<<vb, kLmkThreads, 0, st>>>(n, stride, k1, ld, cur);
             nl += 1;
-            for (int j = 0; j < k2; ++j) {
+            for (int j = k1; j < k; ++j) {
                 k_lmk_argmax<<<ab, kLmkThreads, 0, st>>>(n, cur, keys + j);
-                k_lmk_take<<<vb, kLmkThreads, 0, st>>>(n, stride, k1, ld, cur, keys + j, d_ids, k1 + j);
+                k_lmk_take<<<vb, kLmkThreads, 0, st>>>(n, stride, k1, ld, cur, keys + j, d_ids, j);
                 nl += 2;
             }
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = cudaMemsetAsync(visited, 0, 2 * masks, st);
+    }
+    // later rounds: slots r1.. in groups of 64, from their vertices in d_ids
+    for (int s0 = r1; e == cudaSuccess && s0 < k; s0 += 64) {
+        const int cnt = k - s0 < 64 ? k - s0 : 64;
+        e = cudaMemsetAsync(visited, 0, 2 * masks, st);
         if (e == cudaSuccess) {
-            k_lmk_seed<<<1, 64, 0, st>>>(n, k2, k1, stride, d_ids, visited, fa, ld);
+            k_lmk_seed<<<1, 64, 0, st>>>(n, s0, cnt, stride, d_ids, visited, fa, ld);
             nl += 1;
-            e = lmk_round(n, rp, col, stride, k2 == 64 ? ~0ull : ((1ull << k2) - 1), k1, ld, visited, fa, fb, changed,
-                          st, &nl);
+            e = lmk_round(n, rp, col, stride, cnt == 64 ? ~0ull : ((1ull << cnt) - 1), s0, ld, visited, fa, fb,
+                          changed, st, &nl);
         }
     }
     if (e == cudaSuccess && ids) {
-        for (int j = 0; j < 64; ++j) ids[j] = j < k1 && j < n ? j : -1;
-        if (k2 > 0) {
-            e = cudaMemcpyAsync(ids + k1, d_ids + k1, (size_t)k2 * 4, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        }
+        e = cudaMemcpyAsync(h_ids, d_ids, sizeof(h_ids), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess)
+            for (int j = 0; j < kLmkMax; ++j) ids[j] = j < k ? h_ids[j] : -1;
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     const int rc = e == cudaSuccess ? PSPC_OK : cuda_status(e);

@@ -615,7 +615,7 @@ __device__ int landmark_filter(const LevelArgs& A, const uint32_t* s_lmk, int d,
             // two uint16 distances per word; 0xFFFF (undefined) saturates
             // the sum and is masked out of the difference test
 #pragma unroll
-            for (int w = 0; w < 8; ++w)
+            for (int w = 0; w < kLmkMax / 8; ++w)
                 if (w < words) {
                     const uint4 b4 = __ldg(row + w);
                     const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
@@ -676,7 +676,7 @@ template <int kMap, bool kOffChip, int NT>
 __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_item, s_nkeys, s_abort, s_m, s_next, s_nsurv, s_kept;
-    __shared__ uint32_t s_lmk[32];  // u's landmark distances (uint16 pairs)
+    __shared__ uint32_t s_lmk[kLmkMax / 2];  // u's landmark distances (uint16 pairs)
     __shared__ uint64_t s_useg[kUSideLevels];  // u's level descriptors for the rule-2 scan
     __shared__ int s_wcnt[NT / 32];
     __shared__ unsigned long long s_base;
@@ -1107,7 +1107,7 @@ __device__ __forceinline__ void add_count(uint64_t& sum, uint32_t& flag, uint64_
 __global__ void __launch_bounds__(kMicroThreads) k_level_micro(const LevelArgs A) {
     __shared__ uint32_t s_hub[kMicroWarps][64];
     __shared__ unsigned long long s_cnt[kMicroWarps][64];
-    __shared__ uint32_t s_lmkw[kMicroWarps][32];
+    __shared__ uint32_t s_lmkw[kMicroWarps][kLmkMax / 2];
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int d = A.d;
@@ -1263,7 +1263,7 @@ __global__ void __launch_bounds__(kMicroThreads) k_level_micro(const LevelArgs A
         if (d >= 3 && uniq > 0) {
             bool und[2] = {cand[0], cand[1]};
             if (A.lmk) {
-                if (lane < A.lmk_stride / 4) ul[lane] = __ldg((const uint32_t*)(A.lmk + u * A.lmk_stride) + lane);
+                for (int i = lane; i < A.lmk_stride / 4; i += 32) ul[i] = __ldg((const uint32_t*)(A.lmk + u * A.lmk_stride) + i);
                 __syncwarp();
                 const uint32_t dd = (uint32_t)d * 0x00010001u;
 #pragma unroll

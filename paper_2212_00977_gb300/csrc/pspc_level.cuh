@@ -91,7 +91,7 @@ struct LevelArgs {
     uint8_t* gscratch;    // per-CTA table memory when the tables are off chip
     size_t gscratch_stride;
     const uint8_t* lmk;   // [n][lmk_stride] bytes of uint16 landmark distances, or NULL (no filter)
-    int lmk_stride;       // bytes per row: a multiple of 16, <= 128
+    int lmk_stride;       // bytes per row: a multiple of 16, <= 2 kLmkMax
     int lmk_words;        // 16-byte words of each row the filter tests at this level
 };
 

@@ -90,7 +90,7 @@ GRAPHS = {
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
-@pytest.mark.parametrize("k", [1, 17, 32, 64])
+@pytest.mark.parametrize("k", [1, 17, 32, 64, 100, 128])
 def test_landmark_distances_equal_bfs(pspc, name, k):
     g, rank = GRAPHS[name]()
     ix = pspc.Index.from_graph(g, rank, landmarks=k)
@@ -161,7 +161,7 @@ def test_batch_landmarks_per_graph(pspc):
 
 
 @pytest.mark.parametrize("name", ["ba2000", "rmat12_ef16", "grid64"])
-@pytest.mark.parametrize("k", [-1, 1, 17, 64])
+@pytest.mark.parametrize("k", [-1, 1, 17, 64, 128])
 def test_index_independent_of_landmarks(pspc, name, k):
     g, rank = GRAPHS[name]()
     ref = oracle.OracleIndex(g, rank).export()
@@ -179,7 +179,11 @@ def test_index_independent_of_landmarks(pspc, name, k):
 
 def test_landmark_option_range(pspc):
     g, rank = GRAPHS["ba2000"]()
-    for bad in (-2, 65):
+    graphs = [(n, rp, col, rk) for n, rp, col, rk in P.ba_batch(count=3, n_range=(20, 40), m_range=(1, 2), seed=3)]
+    with pytest.raises(pspc.PSPCError) as e:
+        pspc.Index.build_batch(graphs, landmarks=65)
+    assert e.value.code == 1
+    for bad in (-2, 129):
         with pytest.raises(pspc.PSPCError) as e:
             pspc.Index.from_graph(g, rank, landmarks=bad)
         assert e.value.code == 1
