@@ -60,6 +60,7 @@ constexpr int kProbeUnroll = 4;  // loads in flight per lane in the prune scan
 constexpr uint32_t kSegCacheMinWords = 1024;  // narrowest useful level cache (32K ids)
 constexpr uint32_t kSegCacheMaxWords = 8192;  // widest (the off-chip tables can be far larger)
 constexpr int kGatherUnroll = 4; // loads in flight per lane in the pull
+constexpr unsigned kRouteSamples = 64;  // on-chip attempts per size class before routing by their outcome
 constexpr uint32_t kPrunedBit = 0x80000000u;  // list entry: candidate pruned by rule 2
 constexpr uint32_t kProvenBit = 0x40000000u;  // list entry: survival proven by the landmarks
 constexpr uint32_t kSlotMask = 0x3FFFFFFFu;
@@ -675,7 +676,7 @@ __device__ void block_bitonic_sort(unsigned long long* buf, uint32_t P) {
 template <int kMap, bool kOffChip, int NT>
 __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_item, s_nkeys, s_abort, s_m, s_next, s_nsurv, s_kept;
+    __shared__ int s_item, s_nkeys, s_abort, s_m, s_next, s_nsurv, s_kept, s_route;
     __shared__ uint32_t s_lmk[kLmkMax / 2];  // u's landmark distances (uint16 pairs)
     __shared__ uint64_t s_useg[kUSideLevels];  // u's level descriptors for the rule-2 scan
     __shared__ int s_wcnt[NT / 32];
@@ -715,6 +716,32 @@ __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelA
         // to the final off-chip pass, whose slabs hold the full bound.
         const uint32_t full_cap = cand_cap_for(raw, u, A.cap_c_max);
         uint32_t cap_c = (kOffChip && A.off_start_cap) ? min(full_cap, A.off_start_cap) : full_cap;
+        // A vertex whose bound does not fit the on-chip table may overflow
+        // it; an overflowing attempt reads about half its entries for
+        // nothing. Once at least kRouteSamples such attempts in its size
+        // class (floor(log2 pulled entries)) have been made at this level
+        // and more than two thirds overflowed, it goes to the off-chip pass
+        // without an attempt (the same labels either way).
+        const bool may_overflow = !kOffChip && full_cap >= A.cap_c_max;
+        const int rb = 63 - __clzll((unsigned long long)raw | 1ull);
+        if (may_overflow) {
+            if (tid == 0) {
+                const unsigned a = *(volatile unsigned*)&A.stt->route_att[rb];
+                const unsigned o = *(volatile unsigned*)&A.stt->route_ovf[rb];
+                s_route = a >= kRouteSamples && 3ull * o > 2ull * a;
+                if (s_route) {
+                    const int p = atomicAdd(&A.stt->n_retry, 1);
+                    A.retry_list[p] = (int32_t)u;
+                    atomicMax(&A.stt->need_cap_c, (unsigned long long)cand_cap_for(raw, u, 1u << 30));
+                    atomicMax(&A.stt->need_cap_u, (unsigned long long)label_cap_for(A.lab_size[u]));
+                }
+            }
+            __syncthreads();
+            if (s_route) {
+                __syncthreads();  // s_route and s_item are rewritten by the next item
+                continue;
+            }
+        }
 
         BitMap bm;
         HashMap hm;
@@ -883,6 +910,10 @@ __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelA
                 if (kOffChip) {
                     A.giant_list[atomicAdd(&A.stt->n_giant, 1)] = (int32_t)u;
                 } else {
+                    if (may_overflow) {
+                        atomicAdd(&A.stt->route_att[rb], 1u);
+                        atomicAdd(&A.stt->route_ovf[rb], 1u);
+                    }
                     const int p = atomicAdd(&A.stt->n_retry, 1);
                     A.retry_list[p] = (int32_t)u;
                     atomicMax(&A.stt->need_cap_c, (unsigned long long)cand_cap_for(raw, u, 1u << 30));
@@ -1080,6 +1111,7 @@ __global__ void __launch_bounds__(NT, level_min_blocks(NT)) k_level(const LevelA
             }
         }
         if (tid == 0) atomicAdd(&A.stt->unique_total, (unsigned long long)s_nkeys);
+        if (tid == 0 && may_overflow) atomicAdd(&A.stt->route_att[rb], 1u);
         __syncthreads();
     }
 }

@@ -51,6 +51,11 @@ struct LevelStatus {
     int n_giant;     // off-chip vertices whose candidates overflow the slab
     int work_giant;
     int work_micro;
+    // on-chip attempts and overflows of vertices that can overflow, by
+    // floor(log2 pulled entries): where most overflow, the rest go straight
+    // to the off-chip pass
+    unsigned int route_att[kBuckets];
+    unsigned int route_ovf[kBuckets];
     int bucket_cnt[kBuckets];
     int bucket_base[kBuckets];
     int bucket_fill[kBuckets];
