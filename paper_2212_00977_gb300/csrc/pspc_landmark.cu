@@ -19,7 +19,10 @@
 // the first round's landmarks and (b) the landmark lower bound
 // max_j |sd(v,l_j) - sd(p,l_j)| of its distance to every spread landmark p
 // chosen before it (ties to the smaller id), so it is far from all of
-// them; a second round of searches gives their distances.
+// them; a second round of searches gives their distances. When no vertex
+// is farther than D from the first landmarks and 2D < kLmkDeepLevel, the
+// labels they cover stop short of the levels that test spread landmarks,
+// and none are placed.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -84,15 +87,24 @@ __global__ void __launch_bounds__(kLmkThreads)
 
 // Spread landmarks. cur[v]: the score of v (the smaller of its distance to
 // the first round's k1 landmarks and its lower bounds to the spread ones
-// chosen so far); 0 for vertices no first-round landmark reached.
-__global__ void k_lmk_score(int64_t n, int stride, int k1, const uint8_t* __restrict__ ld, uint32_t* __restrict__ cur) {
+// chosen so far); 0 for vertices no first-round landmark reached. dmax: the
+// largest distance of any vertex from a first-round landmark.
+__global__ void k_lmk_score(int64_t n, int stride, int k1, const uint8_t* __restrict__ ld, uint32_t* __restrict__ cur,
+                            unsigned* __restrict__ dmax) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const uint16_t* r = (const uint16_t*)(ld + v * stride);
-    uint32_t m = 0xFFFFFFFFu;
-    for (int j = 0; j < k1; ++j)
-        if (r[j] != 0xFFFFu) m = min(m, (uint32_t)r[j]);
-    cur[v] = m == 0xFFFFFFFFu ? 0u : m;
+    uint32_t m = 0xFFFFFFFFu, far = 0;
+    if (v < n) {
+        const uint16_t* r = (const uint16_t*)(ld + v * stride);
+        for (int j = 0; j < k1; ++j)
+            if (r[j] != 0xFFFFu) {
+                m = min(m, (uint32_t)r[j]);
+                far = max(far, (uint32_t)r[j]);
+            }
+        cur[v] = m == 0xFFFFFFFFu ? 0u : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) far = max(far, __shfl_xor_sync(0xFFFFFFFFu, far, o));
+    if ((threadIdx.x & 31) == 0 && far) atomicMax(dmax, far);
 }
 
 // The largest score, ties to the smaller id: key = score << 32 | ~v.
@@ -196,15 +208,28 @@ int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t
     if (e == cudaSuccess)
         e = lmk_round(n, rp, col, stride, r1 == 64 ? ~0ull : ((1ull << r1) - 1), 0, ld, visited, fa, fb, changed, st,
                       &nl);
-    if (e == cudaSuccess && k1 < k) {  // spread landmarks, from the first round's distances (k1 <= 64)
+    // Spread landmarks, from the first round's distances (k1 <= 64). The
+    // filter tests them from level kLmkDeepLevel on; when every distance
+    // from the first landmarks is at most D with 2D < kLmkDeepLevel, labels
+    // between vertices they reach stop short of that level, and the spread
+    // ones are left out (slots k1..k-1 stay empty).
+    int kk = k;
+    if (e == cudaSuccess && k1 < k) {
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const unsigned ab = (unsigned)std::min<int64_t>(vb, std::max(sms, 1) * 4);
         if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, kLmkMax * 8, st);
+        unsigned dmax = 0;
+        if (e == cudaSuccess) e = cudaMemsetAsync(changed, 0, sizeof(unsigned), st);
         if (e == cudaSuccess) {
-            k_lmk_score<<<vb, kLmkThreads, 0, st>>>(n, stride, k1, ld, cur);
+            k_lmk_score<<<vb, kLmkThreads, 0, st>>>(n, stride, k1, ld, cur, (unsigned*)changed);
             nl += 1;
+            e = cudaMemcpyAsync(&dmax, changed, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess && 2 * dmax < (unsigned)kLmkDeepLevel) kk = k1;
+        }
+        if (e == cudaSuccess && kk > k1) {
             for (int j = k1; j < k; ++j) {
                 k_lmk_argmax<<<ab, kLmkThreads, 0, st>>>(n, cur, keys + j);
                 k_lmk_take<<<vb, kLmkThreads, 0, st>>>(n, stride, k1, ld, cur, keys + j, d_ids, j);
@@ -214,8 +239,8 @@ int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t
         }
     }
     // later rounds: slots r1.. in groups of 64, from their vertices in d_ids
-    for (int s0 = r1; e == cudaSuccess && s0 < k; s0 += 64) {
-        const int cnt = k - s0 < 64 ? k - s0 : 64;
+    for (int s0 = r1; e == cudaSuccess && s0 < kk; s0 += 64) {
+        const int cnt = kk - s0 < 64 ? kk - s0 : 64;
         e = cudaMemsetAsync(visited, 0, 2 * masks, st);
         if (e == cudaSuccess) {
             k_lmk_seed<<<1, 64, 0, st>>>(n, s0, cnt, stride, d_ids, visited, fa, ld);
@@ -228,7 +253,7 @@ int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t
         e = cudaMemcpyAsync(h_ids, d_ids, sizeof(h_ids), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e == cudaSuccess)
-            for (int j = 0; j < kLmkMax; ++j) ids[j] = j < k ? h_ids[j] : -1;
+            for (int j = 0; j < kLmkMax; ++j) ids[j] = j < kk ? h_ids[j] : -1;
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     const int rc = e == cudaSuccess ? PSPC_OK : cuda_status(e);

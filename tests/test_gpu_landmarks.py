@@ -40,13 +40,15 @@ def expected_landmark_vertices(g, rank, k):
     vertices, each maximising the smaller of its distance to the first 32
     and its landmark lower bound to the spread ones before it (0 for a
     vertex no first landmark reaches; 0xFFFF when exactly one of the two is
-    reached by some first landmark), ties to the higher rank. Distances from
-    oracle BFS."""
+    reached by some first landmark), ties to the higher rank; none when no
+    vertex is 8 or more from the first 32. Distances from oracle BFS."""
     order = _order(rank)
     k1 = k if (k <= 32 or g.n <= 4 * k) else 32
     ids = [int(order[j]) for j in range(min(k1, g.n))]
     if k1 < k:
         D = np.stack([oracle.bfs_count(g, v)[0] for v in ids]).astype(np.int64)
+        if 2 * D.max() < 16:  # labels stop short of the levels that test spread landmarks
+            return ids + [-1] * (k - len(ids))
         R = D >= 0
         score = np.where(R.any(axis=0), np.where(R, D, 1 << 40).min(axis=0), 0)
         for _ in range(k - k1):
