@@ -157,6 +157,9 @@ typedef struct {
     int64_t offchip_vertices;  /* vertices whose tables did not fit on chip
                                   and ran in device memory */
     float offchip_ms;          /* device time of their kernel launches */
+    int64_t routed_vertices;   /* of those, vertices sent there without an
+                                  on-chip attempt, their size class having
+                                  mostly overflowed the on-chip table */
 } pspc_level_stat_t;
 
 typedef struct {

@@ -62,7 +62,8 @@ class LevelStat(ctypes.Structure):
                 ("entries", ctypes.c_int64), ("active_vertices", ctypes.c_int64),
                 ("active_arcs", ctypes.c_int64), ("ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                 ("landmark_pruned", ctypes.c_int64), ("landmark_proven", ctypes.c_int64),
-                ("offchip_vertices", ctypes.c_int64), ("offchip_ms", ctypes.c_float)]
+                ("offchip_vertices", ctypes.c_int64), ("offchip_ms", ctypes.c_float),
+                ("routed_vertices", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):

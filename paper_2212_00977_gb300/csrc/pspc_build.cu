@@ -1246,6 +1246,8 @@ struct Builder {
                 keep.arena_overflow = 0;
                 keep.work_smem = keep.work_global = keep.work_light = keep.work_giant = keep.work_micro = 0;
                 keep.n_giant = 0;
+                memset(keep.route_att, 0, sizeof(keep.route_att));  // the level is re-run from scratch
+                memset(keep.route_ovf, 0, sizeof(keep.route_ovf));
                 cudaMemcpyAsync(stt, &keep, sizeof(LevelStatus), cudaMemcpyHostToDevice, st);
                 *hstt = keep;
             }
@@ -1268,6 +1270,11 @@ struct Builder {
             ls.landmark_proven = (long long)hstt->lmk_proven;
             ls.offchip_vertices = n_off;
             ls.offchip_ms = offchip_ms;
+            // the retry list holds the overflowed attempts (counted per size
+            // class) and the routed vertices
+            long long ovf_attempts = 0;
+            for (int b = 0; b < kBuckets; ++b) ovf_attempts += hstt->route_ovf[b];
+            ls.routed_vertices = std::max(0LL, (long long)hstt->n_retry - ovf_attempts);
             out.lstats.push_back(ls);
             if (o.verbose)
                 fprintf(stderr, "pspc level %d: raw %lld unique %lld entries %lld active %d (off-chip %d) %.3f ms\n",

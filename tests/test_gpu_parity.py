@@ -258,6 +258,21 @@ def test_rmat16_full_size(pspc):
     assert ix.stats()["entries"] == len(hub)
 
 
+def test_rmat16_small_tables_routing(pspc):
+    """R-MAT scale 16 with on-chip candidate tables of 1,024 slots: most
+    heavy vertices of levels 2-4 overflow them, so whole size classes are
+    routed to the off-chip pass without an attempt; every entry of the
+    index against the definition, as with the default tables."""
+    g, rank, pairs_fn = P.workload("rmat16")
+    ix = gpu_index(pspc, g, rank, cand_capacity=1024)
+    ls = ix.level_stats()
+    assert sum(l["routed_vertices"] for l in ls) > 1000
+    assert all(l["routed_vertices"] <= l["offchip_vertices"] for l in ls)
+    off, hub, dist, cnt, ovf = ix.export()
+    _check_whole_index(g, rank, off, hub, dist, cnt, ovf)
+    ix.free()
+
+
 def _check_whole_index(g, rank, off, hub, dist, cnt, ovf):
     """Every entry of an exported index equals the definition (all hub
     columns), and labels are strictly increasing in hub rank and end with
