@@ -326,6 +326,8 @@ struct FinArgs {
     unsigned long long* n_ovf;
     unsigned long long* gscratch;
     size_t gscratch_stride;  // keys per CTA
+    const int32_t* comp_base;  // batches: first id of each vertex's graph (NULL: 0)
+    uint32_t rank_words;       // k_finalize_rank: bitmap words per CTA
 };
 
 // Exclusive scan of one value per thread of a kFinThreads block into pre[];
@@ -422,6 +424,81 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinArgs F) {
         if (novf) atomicAdd(&s_ovf, novf);
         __syncthreads();
     }
+    __syncthreads();
+    if (tid == 0 && s_ovf) atomicAdd(F.n_ovf, s_ovf);
+}
+
+// Many levels: each level segment of a vertex is hub-sorted, and its hubs
+// are distinct ids in [cbase, u] (ranked above u, or u itself). The final
+// slot of an entry is the number of the vertex's hubs below it: a bitmap of
+// them over ids cbase..u on chip, its popcount prefix, then every entry is
+// written at its rank, with its level as the distance and its count read
+// in segment order (no sort, no gather of counts, no level search).
+constexpr uint32_t kFinRankWords = 12288;  // ids up to 393,216 per graph
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize_rank(const FinArgs F) {
+    extern __shared__ __align__(16) uint32_t s_bits[];  // rank_words bitmap words, then their prefixes
+    __shared__ int s_pre[kFinThreads];
+    __shared__ int s_wtot[kFinThreads / 32];
+    __shared__ uint64_t s_st[kFinThreads];
+    __shared__ unsigned long long s_ovf;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_ovf = 0;
+    uint32_t* bits = s_bits;
+    uint32_t* wp = s_bits + F.rank_words;
+    unsigned long long novf = 0;
+    for (int64_t u = blockIdx.x; u < F.n; u += gridDim.x) {
+        const int64_t o0 = F.off[u];
+        const uint32_t cb = F.comp_base ? (uint32_t)__ldg(F.comp_base + u) : 0u;
+        const uint32_t W = (uint32_t)((u - cb) >> 5) + 1;
+        for (uint32_t i = tid; i < W; i += kFinThreads) bits[i] = 0u;
+        __syncthreads();
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {  // popcount prefix of the bitmap, a run of words per thread
+                const uint32_t per = (W + kFinThreads - 1) / kFinThreads;
+                const uint32_t w0 = tid * per < W ? tid * per : W, w1 = w0 + per < W ? w0 + per : W;
+                uint32_t v = 0;
+                for (uint32_t i = w0; i < w1; ++i) v += __popc(bits[i]);
+                fin_block_scan(v, s_pre, s_wtot);
+                uint32_t run = (uint32_t)s_pre[tid];
+                for (uint32_t i = w0; i < w1; ++i) {
+                    wp[i] = run;
+                    run += __popc(bits[i]);
+                }
+                __syncthreads();
+            }
+            // the level descriptors kFinThreads at a time, prefix-summed
+            for (int l0 = 0; l0 < F.levels; l0 += kFinThreads) {
+                const int l = l0 + tid;
+                const uint64_t sd = l < F.levels ? F.seg[(int64_t)l * F.n + u] : 0ull;
+                const int total = fin_block_scan(seg_len(sd), s_pre, s_wtot);
+                s_st[tid] = seg_start(sd);
+                __syncthreads();
+                for (int i = tid; i < total; i += kFinThreads) {
+                    int lo = 0, hi = kFinThreads - 1;  // last level j of the chunk with s_pre[j] <= i
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_pre[mid] <= i) lo = mid; else hi = mid - 1;
+                    }
+                    const uint64_t pos = s_st[lo] + (uint64_t)(i - s_pre[lo]);
+                    const uint32_t hw = __ldg(F.hub_arena + pos);
+                    const uint32_t r = (hw & kHubMask) - cb;
+                    if (pass == 0) {
+                        atomicOr(&bits[r >> 5], 1u << (r & 31));
+                    } else {
+                        const uint32_t rank = wp[r >> 5] + __popc(bits[r >> 5] & ((1u << (r & 31)) - 1u));
+                        const uint32_t ovf = hw >> 31;
+                        novf += ovf;
+                        F.hub[o0 + rank] = (int32_t)(hw & kHubMask);
+                        F.dist[o0 + rank] = (uint16_t)((uint32_t)(l0 + lo) | (ovf << 15));
+                        F.cnt[o0 + rank] = __ldg((const unsigned long long*)F.cnt_arena + pos);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (novf) atomicAdd(&s_ovf, novf);
     __syncthreads();
     if (tid == 0 && s_ovf) atomicAdd(F.n_ovf, s_ovf);
 }
@@ -1337,7 +1414,18 @@ struct Builder {
         F.dist = out.dist;
         F.cnt = out.cnt;
         F.n_ovf = n_ovf;
-        if (L <= kFinMergeLevels) {
+        const uint32_t rank_words = (uint32_t)((max_comp + 31) / 32 + 1);
+        const bool by_rank = L > kFinMergeLevels && rank_words <= kFinRankWords;
+        if (by_rank) {  // every vertex, whatever its label size
+            F.comp_base = comp_base;
+            F.rank_words = rank_words;
+            const size_t fin_smem = (size_t)rank_words * 8;
+            PSPC_TRY_CUDA(cudaFuncSetAttribute(k_finalize_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)fin_smem));
+            int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
+            if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
+            k_finalize_rank<<<grid, kFinThreads, fin_smem, st>>>(F);
+        } else if (L <= kFinMergeLevels) {
             const size_t fin_smem = (size_t)kFinSmemKeys * 4;
             PSPC_TRY_CUDA(cudaFuncSetAttribute(k_finalize_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)fin_smem));
@@ -1354,7 +1442,7 @@ struct Builder {
         }
         out.launches += 1;
         PSPC_TRY_CUDA(cudaGetLastError());
-        if (hbig[0] > 0) {
+        if (hbig[0] > 0 && !by_rank) {
             // Labels longer than the on-chip buffer: sort them in device memory.
             int64_t maxT = 0;
             std::vector<int32_t> hb(hbig[0]);
