@@ -328,6 +328,7 @@ struct FinArgs {
     size_t gscratch_stride;  // keys per CTA
     const int32_t* comp_base;  // batches: first id of each vertex's graph (NULL: 0)
     uint32_t rank_words;       // k_finalize_rank: bitmap words per CTA
+    int merge_keys;            // k_finalize_merge: hub words on chip (longer labels are skipped)
 };
 
 // Exclusive scan of one value per thread of a kFinThreads block into pre[];
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_rank(const FinArgs F) 
 constexpr int kFinMergeLevels = 16;
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize_merge(const FinArgs F) {
-    extern __shared__ __align__(16) uint32_t s_hub[];  // kFinSmemKeys hub words
+    extern __shared__ __align__(16) uint32_t s_hub[];  // F.merge_keys hub words
     __shared__ unsigned long long s_st[kFinMergeLevels];
     __shared__ int s_off[kFinMergeLevels + 1];
     __shared__ unsigned long long s_ovf;
@@ -518,10 +519,13 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_merge(const FinArgs F)
     const int L = F.levels;
     if (tid == 0) s_ovf = 0;
     unsigned long long novf = 0;
-    for (int64_t u = blockIdx.x; u < F.n; u += gridDim.x) {
+    // every vertex, or (F.list) the long labels with a larger on-chip buffer
+    const int64_t items = F.list ? (int64_t)F.n_list : F.n;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int64_t u = F.list ? (int64_t)F.list[it] : it;
         const int64_t o0 = F.off[u];
         const int T = (int)(F.off[u + 1] - o0);
-        if (T > kFinSmemKeys) continue;  // uniform: sorted by the off-chip pass
+        if (T > F.merge_keys) continue;  // uniform: placed by a later launch
         if (T == 1) {  // only (u, 0, 1): an isolated vertex, no merge
             if (tid == 0) {
                 const uint64_t s = __ldg(F.seg + u);
@@ -1428,9 +1432,10 @@ struct Builder {
         } else if (L <= kFinMergeLevels) {
             const size_t fin_smem = (size_t)kFinSmemKeys * 4;
             PSPC_TRY_CUDA(cudaFuncSetAttribute(k_finalize_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)fin_smem));
+                                               (int)(2 * fin_smem)));
             int grid = (int)std::min<int64_t>(n, (int64_t)sms * 8);
             if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
+            F.merge_keys = kFinSmemKeys;
             k_finalize_merge<<<grid, kFinThreads, fin_smem, st>>>(F);
         } else {
             const size_t fin_smem = (size_t)kFinSmemKeys * 8;
@@ -1442,7 +1447,23 @@ struct Builder {
         }
         out.launches += 1;
         PSPC_TRY_CUDA(cudaGetLastError());
-        if (hbig[0] > 0 && !by_rank) {
+        // Long labels of a few-level index: the merge again, with twice the
+        // on-chip buffer, over those vertices only.
+        const bool big_by_merge = hbig[0] > 0 && !by_rank && L <= kFinMergeLevels &&
+                                  out.max_label <= 2 * (int64_t)kFinSmemKeys;
+        if (big_by_merge) {
+            int grid = std::min(hbig[0], sms * 2);
+            if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
+            F.list = big;
+            F.n_list = hbig[0];
+            F.merge_keys = 2 * kFinSmemKeys;
+            k_finalize_merge<<<grid, kFinThreads, (size_t)kFinSmemKeys * 8, st>>>(F);
+            F.list = nullptr;
+            F.n_list = 0;
+            out.launches += 1;
+            PSPC_TRY_CUDA(cudaGetLastError());
+        }
+        if (hbig[0] > 0 && !by_rank && !big_by_merge) {
             // Labels longer than the on-chip buffer: sort them in device memory.
             int64_t maxT = 0;
             std::vector<int32_t> hb(hbig[0]);

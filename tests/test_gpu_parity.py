@@ -273,6 +273,21 @@ def test_rmat16_small_tables_routing(pspc):
     ix.free()
 
 
+def test_long_labels_few_levels(pspc):
+    """K(2, 8500) with the middle ranked first: three levels, and the two
+    outer vertices hold labels of 8,501 entries, more than the finalize
+    keeps on chip by default (they are merged again with a larger buffer);
+    every entry against the definition, labels in strict hub order."""
+    m = 8500
+    g = G.bipartite_2m(m)
+    rank = np.arange(g.n, dtype=np.int32)
+    ix = gpu_index(pspc, g, rank)
+    assert ix.label_sizes([m, m + 1]).min() == m + 1
+    off, hub, dist, cnt, ovf = ix.export()
+    _check_whole_index(g, rank, off, hub, dist, cnt, ovf)
+    ix.free()
+
+
 def _check_whole_index(g, rank, off, hub, dist, cnt, ovf):
     """Every entry of an exported index equals the definition (all hub
     columns), and labels are strictly increasing in hub rank and end with
