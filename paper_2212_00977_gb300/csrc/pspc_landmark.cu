@@ -201,7 +201,7 @@ int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t
     for (int j = 0; j < kLmkMax; ++j) h_ids[j] = j < k1 && j < n ? j : -1;
     int64_t nl = 1;
     const unsigned vb = (unsigned)((n + kLmkThreads - 1) / kLmkThreads);
-    // round 1: the first (up to 64) highest-ranked vertices of every graph
+    // first search batch: the first (up to 64) highest-ranked vertices of every graph
     const int r1 = k1 < 64 ? k1 : 64;
     k_lmk_init<<<vb, kLmkThreads, 0, st>>>(n, r1, stride, comp_base, visited, fa, ld);
     e = cudaMemcpyAsync(d_ids, h_ids, sizeof(h_ids), cudaMemcpyHostToDevice, st);
@@ -238,7 +238,7 @@ int landmark_bfs(int64_t n, const int64_t* rp, const int32_t* col, const int32_t
             e = cudaGetLastError();
         }
     }
-    // later rounds: slots r1.. in groups of 64, from their vertices in d_ids
+    // later search batches: slots r1.. in groups of 64, from their vertices in d_ids
     for (int s0 = r1; e == cudaSuccess && s0 < kk; s0 += 64) {
         const int cnt = kk - s0 < 64 ? kk - s0 : 64;
         e = cudaMemsetAsync(visited, 0, 2 * masks, st);
